@@ -1,0 +1,346 @@
+"""Throughput of the first-level J/psi event selection on GB300.
+
+One step = one pass of the whole hot path over one batch: the counting pass
+(triplet formation, fit and cut, chaining, accept bits), the scan of per-unit
+counts and the triplet-writing pass, i.e. a jpsi_run call.  The default batch
+is the 10^6-event Poisson(100) workload (4 stations x 3 layers, ~1 200 hits
+per event, 14.4 GB of FP32 hits, far larger than L2), synthetic and seeded.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank processes its own
+10^6 events (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s on 1 GB300 (bit-exact accept bits), batched vs plain; p50/p99 latency"
+UNIT = "events/s"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("jpsi_kernels.cu", "jpsi_device.cuh", "jpsi_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1810_11966_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per event of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_event"])
+
+
+def algorithmic_bytes(n_events, n_hits, S):
+    """Bytes the counting kernel must move at least: every hit read once (12 B),
+    the CSR offsets (4 B each), per-unit counts (4 B), track count (4 B) and the
+    per-event class byte."""
+    return 12 * n_hits + 4 * (n_events * 3 * S + 1) + 4 * n_events * S + 4 * n_events + n_events
+
+
+def cpu_baseline(workload, params_kw, n_events, threads=None):
+    """The oracle as it stands, on the host cores, over a bounded sample."""
+    import oracle
+    import synth
+    threads = threads or (os.cpu_count() or 1)
+    b = synth.generate(workload, 0, n_events)
+    p = oracle.params(**params_kw)
+    t0 = time.perf_counter()
+    r = oracle.run(p, b, triplets=True, n_threads=threads)
+    dt = time.perf_counter() - t0
+    assert r["status"] == 0
+    return {"value": n_events / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"events [0, {n_events}) of {workload}, counts + triplet lists, {threads} threads, "
+                      f"{dt:.2f} s wall"}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the oracle on the host cores, each step a bounded
+    sample of the same workload; rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    threads = os.cpu_count() or 1
+    n = args.ref_events
+    b = synth.generate(w, 0, n)
+    p = oracle.params(**params_kw(args, w))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run(p, b, triplets=True, n_threads=threads)
+        dt = time.perf_counter() - t0
+        assert r["status"] == 0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    v = n * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "events_per_step": n, "stations": w.n_stations, "mode": args.mode},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"events [0, {n}) of {w.name} per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def params_kw(args, w):
+    t = w.window ** 2
+    return {"n_stations": w.n_stations, "mode": 1 if args.mode == "chain" else 0, "t_xz": t, "t_yz": t}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poisson100_1m")
+    ap.add_argument("--events", type=int, default=None, help="events per rank (default: the workload's)")
+    ap.add_argument("--mode", default="chain", choices=["chain", "paper"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-events", type=int, default=100_000)
+    ap.add_argument("--ref-events", type=int, default=40_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0, help="(for ncu) run this many steps and exit")
+    args = ap.parse_args()
+    rank, world, local = dist_info()
+    if args.warmup < 3 and not args.profile_steps:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import paper_1810_11966_gb300 as jp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    jp.load(build_if_missing=True)
+    w = synth.WORKLOADS[args.workload]
+    n_ev = args.events or w.n_events
+    S = w.n_stations
+
+    # host batch in pinned memory (for the end-to-end leg), then resident copies
+    t0 = time.perf_counter()
+    counts = synth.layer_counts(w, rank * n_ev, n_ev)
+    n_hits = int(counts.sum())
+    pin = {k: torch.empty(n_hits, dtype=torch.float32, pin_memory=True) for k in ("x", "y", "z")}
+    host = synth.generate(w, rank * n_ev, n_ev, out={k: v.numpy() for k, v in pin.items()})
+    off_pin = torch.from_numpy(host["offsets"]).pin_memory()
+    gen_s = time.perf_counter() - t0
+    d = {k: pin[k].to(dev) for k in ("x", "y", "z")}
+    d["offsets"] = off_pin.to(dev)
+    torch.cuda.synchronize()
+
+    p = jp.params(**params_kw(args, w))
+    ctx = jp.Context(p, device=local, hbm_budget=64 << 30)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    batch = jp.make_batch(d["x"], d["y"], d["z"], d["offsets"], n_ev, n_hits)
+
+    # outputs, sized by a counting run
+    nu = n_ev * S
+    acc = torch.empty((n_ev + 31) // 32, dtype=torch.int32, device=dev)
+    tc = torch.empty(n_ev, dtype=torch.int32, device=dev)
+    toff = torch.empty(nu + 1, dtype=torch.int64, device=dev)
+    o = jp.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
+    ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))
+    cap = o.trip_needed
+    trip = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
+    o.triplets, o.trip_capacity = trip.data_ptr(), cap
+
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))
+        torch.cuda.synchronize()
+        return
+
+    def timed(run_fn, steps, warmup):
+        for _ in range(warmup):
+            ctx.check(run_fn(ctx.ctx, batch, o, st))
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        jp.jpsi_timing_enable(ctx.ctx, True)
+        evs[0].record(stream)
+        for i in range(steps):
+            ctx.check(run_fn(ctx.ctx, batch, o, st))
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        tm = jp.jpsi_timing_get(ctx.ctx)
+        jp.jpsi_timing_enable(ctx.ctx, False)
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        tot = evs[0].elapsed_time(evs[steps])
+        if pg:
+            t = torch.tensor([tot], dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            tot = float(t[0])
+        return tot, per, tm
+
+    clocks = Clocks(local)
+    clocks.start()
+    tot_b, per_b, tm_b = timed(jp.jpsi_run, args.steps, args.warmup)
+    clk = clocks.stop()
+    tot_p, per_p, tm_p = timed(jp.jpsi_run_plain, max(args.steps // 2, 3), 3)
+
+    # end to end through the public API from pinned host buffers
+    hb = jp.make_batch(pin["x"], pin["y"], pin["z"], off_pin, n_ev, n_hits)
+    h_acc = torch.empty((n_ev + 31) // 32, dtype=torch.int32, pin_memory=True)
+    h_tc = torch.empty(n_ev, dtype=torch.int32, pin_memory=True)
+    h_to = torch.empty(nu + 1, dtype=torch.int64, pin_memory=True)
+    h_tr = torch.empty((max(cap, 1), 3), dtype=torch.int32, pin_memory=True)
+    ho = jp.jpsi_outputs()
+    ho.accept_bits, ho.track_counts, ho.trip_off, ho.triplets = (h_acc.data_ptr(), h_tc.data_ptr(), h_to.data_ptr(),
+                                                                 h_tr.data_ptr())
+    ho.trip_capacity = cap
+    for _ in range(2):
+        ctx.check(jp.jpsi_run_host(ctx.ctx, hb, ho, st))
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        ctx.check(jp.jpsi_run_host(ctx.ctx, hb, ho, st))
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_mean = sum(e2e_t) / len(e2e_t)
+    h2d = 12 * n_hits + 4 * (n_ev * 3 * S + 1)
+    d2h = 4 * ((n_ev + 31) // 32) + 4 * n_ev + 8 * (nu + 1) + 12 * cap
+    assert np.array_equal(h_tc.numpy(), tc.cpu().numpy())
+
+    ms_b = tot_b / args.steps
+    ms_p = tot_p / len(per_p)
+    value = world * n_ev / (ms_b / 1000.0)
+    light_ms = tm_b.light_ms / max(tm_b.runs, 1)
+    alg = algorithmic_bytes(n_ev, n_hits, S)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (light_ms / 1000.0) / 1e9
+    tpe = ncu_traffic("k_light_count", w.name)
+    per_sorted = sorted(per_b)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_events": n_ev, "stations": S, "mean_hits_per_event": n_hits / n_ev,
+                   "mode": args.mode, "window_cm": w.window, "form": "batched (persistent kernels + CUDA graph)",
+                   "l2": f"inputs ({12 * n_hits / 1e9:.1f} GB) larger than L2; no flush", "seed": w.seed},
+        "hits_per_s": world * n_hits / (ms_b / 1000.0),
+        "plain": {"value": world * n_ev / (ms_p / 1000.0), "ms_per_step": ms_p},
+        "latency_ms": {"p50": per_sorted[len(per_sorted) // 2],
+                       "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
+        "phases_ms": {"light_count": light_ms, "count_rest": tm_b.count_rest_ms / max(tm_b.runs, 1),
+                      "emit": tm_b.emit_ms / max(tm_b.runs, 1)},
+        "roofline": {"bound": "hbm", "kernel": "k_light_count", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None if tpe is None else tpe * n_ev,
+                     "algorithmic_bytes": alg},
+        "e2e": {"value": world * n_ev / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1000 * e2e_mean},
+        "gpu_launches": int(tm_b.kernel_launches),
+        "clocks": clk,
+        "triplets_per_step": cap,
+        "generate_s": gen_s,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), min(args.cpu_events, n_ev))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * libjpsi -- GB300 (sm_103a) first-level J/psi event selection in the CBM
+ * muon chambers, after V. Singhal, S. Chattopadhyay, V. Friese,
+ * "Investigation of heterogeneous computing platforms for real-time data
+ * analysis in the CBM experiment", arXiv:1810.11966.
+ *
+ * The operation (Sec. 3.2, steps 1-3): for every event, form all triplets of
+ * hits of a station with one hit from each of its three layers; fit each
+ * triplet together with the event vertex (0, 0) by straight lines x = m0 z and
+ * y = m1 z; reject the triplet if its mean square deviation per degree of
+ * freedom exceeds a threshold in either plane; select the event if at least
+ * two candidates remain.
+ *
+ *   JPSI_MODE_PAPER  exactly the paper: the trigger station (the last one,
+ *                    Sec. 2) only; candidates = passing trigger triplets.
+ *   JPSI_MODE_CHAIN  an extension: triplets are formed in every station, and a
+ *                    passing trigger triplet T is a track candidate iff every
+ *                    other station holds a passing triplet whose three hits,
+ *                    taken against T's fitted slopes (no refit), have a summed
+ *                    squared residual within the same thresholds in both
+ *                    planes.  With one station it equals PAPER.
+ *
+ * Arithmetic (the reference result).  FP32, every operation rounded to
+ * nearest in this order, no contraction, no flush-to-zero:
+ *     Szz = (z0*z0 + z1*z1) + z2*z2,  Suz = (u0*z0 + u1*z1) + u2*z2,
+ *     m = Suz / Szz,  r_k = u_k - m*z_k,  S_u = (r0*r0 + r1*r1) + r2*r2,
+ *     pass = S_x <= C_xz && S_y <= C_yz,   C = fl32(ndf * t).
+ * "MSD per dof <= t" is read as S <= ndf * t (equality passes; NaN fails).
+ *
+ * Data layout (all device memory, caller-owned unless stated):
+ *   x, y, z   float32 [n_hits], structure of arrays, in cm.
+ *   offsets   int32 [n_events * n_stations * 3 + 1]: hits of layer l of station
+ *             s of event e are [offsets[(e*S+s)*3+l], offsets[(e*S+s)*3+l+1]);
+ *             offsets[0] = 0, non-decreasing, offsets[last] = n_hits.
+ *             Layer 0 is the most upstream layer of its station.
+ *   n_hits < 2^31; every z of a hit that the mode reads must not be <= 0
+ *   (NaN and +Inf coordinates are legal and never pass).
+ *
+ * Outputs (device memory, caller-owned; any pointer may be NULL = not wanted,
+ * except that triplets need trip_off):
+ *   accept_bits   uint32 [(n_events+31)/32]; bit (e & 31) of word e >> 5 is
+ *                 set iff event e has >= min_candidates candidates.
+ *   track_counts  int32 [n_events]: candidates per event.
+ *   trip_off      int64 [n_events*S + 1]: exclusive scan of the passing-triplet
+ *                 counts per unit u = e*S + s (CHAIN: every station; PAPER:
+ *                 the trigger station, other units 0).
+ *   triplets      int32 [3 * trip_capacity]: (i, j, k) layer-local hit indices
+ *                 of every passing triplet, unit u at rows [trip_off[u],
+ *                 trip_off[u+1]); order inside a unit is unspecified.
+ *   trip_needed   set to the total number of passing triplets.
+ *
+ * Errors: every call returns a status; nothing throws across the ABI.  On
+ * JPSI_ECAPACITY the counts, trip_off and accept bits are complete and
+ * trip_needed holds the size to retry with; triplets are unspecified.  On
+ * JPSI_EINVAL / JPSI_ECUDA outputs are unspecified.  Device waits inside the
+ * library are bounded and surface as JPSI_ETIMEOUT.
+ *
+ * Threads: a context is used by one host thread at a time (JPSI_EBUSY
+ * otherwise).  Runs are synchronous with respect to the given stream: the
+ * call returns after the stream has completed the work.
+ */
+#ifndef JPSI_H
+#define JPSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JPSI_OK = 0,
+    JPSI_EINVAL = 1,    /* malformed arguments, offsets or z <= 0 */
+    JPSI_ENOMEM = 2,    /* device/host allocation failed or exceeds the budget */
+    JPSI_ECAPACITY = 3, /* triplet buffer too small; see trip_needed */
+    JPSI_ECUDA = 4,     /* a CUDA call failed */
+    JPSI_ETIMEOUT = 5,  /* a bounded wait ran out */
+    JPSI_EBUSY = 6      /* context in use by another call */
+} jpsi_status;
+
+typedef enum { JPSI_MODE_PAPER = 0, JPSI_MODE_CHAIN = 1 } jpsi_mode;
+
+/* Selection parameters (Sec. 3.2).  Defaults of the paper: ndf = 2 (three
+ * hits, one slope), min_candidates = 2, trigger_station = n_stations - 1,
+ * t_xz = 0.03 and t_yz = 0.025 cm^2 (step 2b). */
+typedef struct {
+    int32_t n_stations;      /* 1 .. 16 */
+    int32_t trigger_station; /* 0 .. n_stations-1 */
+    int32_t mode;            /* jpsi_mode */
+    int32_t ndf;             /* >= 1 */
+    int32_t min_candidates;  /* >= 0 */
+    float t_xz, t_yz;        /* >= 0, finite */
+} jpsi_params;
+
+typedef struct {
+    int64_t n_events;
+    int64_t n_hits;
+    const float *x, *y, *z;
+    const int32_t *offsets;
+} jpsi_batch;
+
+typedef struct {
+    uint32_t *accept_bits;
+    int32_t *track_counts;
+    int64_t *trip_off;
+    int32_t *triplets;
+    int64_t trip_capacity; /* rows of 3 int32 */
+    int64_t trip_needed;   /* out */
+} jpsi_outputs;
+
+typedef struct jpsi_ctx jpsi_ctx;
+
+/* Creates a context on `device`.  hbm_budget bounds the bytes of device
+ * scratch the context may hold (0 = 8 GiB).  The context owns its scratch
+ * (per-unit counts, scan buffers, work queues, graphs, serving slots). */
+jpsi_status jpsi_create(const jpsi_params *params, int device, size_t hbm_budget, jpsi_ctx **out);
+
+/* Releases everything the context owns.  NULL is ignored. */
+void jpsi_destroy(jpsi_ctx *ctx);
+
+/* One-launch form (Sec. 5.3's one-thread-per-event scheme recast as one warp
+ * per event): a static grid with one warp per event; events too large for a
+ * warp's shared-memory tile go to a block-per-event kernel.  `batch` and
+ * `out` point to device memory.  `cuda_stream` is a cudaStream_t (NULL =
+ * legacy default stream). */
+jpsi_status jpsi_run_plain(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
+
+/* Batched form: persistent kernels over an atomic work queue, events split
+ * into light (warp) and heavy (block) work by the autotuned thresholds, the
+ * counting passes replayed from a captured CUDA graph.  Same contract and
+ * bit-identical results as jpsi_run_plain. */
+jpsi_status jpsi_run(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
+
+/* jpsi_run on HOST memory: `batch` and `out` point to host buffers (pinned
+ * for full speed).  The library copies inputs into device buffers it keeps
+ * resident, runs, and copies the outputs back before returning. */
+jpsi_status jpsi_run_host(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
+
+/* Picks the batched form's launch shape (warps per block, events per grab,
+ * light/heavy cutoff) by timing candidates on `sample` (device memory) and
+ * keeps the fastest in the context.  Results do not depend on the choice. */
+jpsi_status jpsi_autotune(jpsi_ctx *ctx, const jpsi_batch *sample);
+
+/* ------------------------------------------------------------ serving
+ * Continuous batching of timeslices.  jpsi_serve_start reserves `n_slots`
+ * resident slots whose device buffers fit `slot_hits` hits, `slot_events`
+ * events and `slot_triplets` triplets each, within the context's budget.
+ * jpsi_serve_submit copies one HOST batch into a free slot on a copy stream
+ * and runs it on one of the compute streams as soon as a slot is free (it
+ * blocks while all slots are busy: back-pressure, nothing is dropped);
+ * outputs are copied back into the HOST `out` buffers, which must stay valid
+ * until jpsi_serve_wait returns for the ticket.  Each result is identical to
+ * jpsi_run on the same batch alone. */
+jpsi_status jpsi_serve_start(jpsi_ctx *ctx, int n_slots, int64_t slot_events, int64_t slot_hits,
+                             int64_t slot_triplets);
+jpsi_status jpsi_serve_submit(jpsi_ctx *ctx, const jpsi_batch *host_batch, jpsi_outputs *host_out,
+                              uint64_t *ticket);
+/* Waits at most timeout_ms (< 0: no limit) for `ticket`; on completion writes
+ * the run's status and its latency (submit -> outputs in host memory). */
+jpsi_status jpsi_serve_wait(jpsi_ctx *ctx, uint64_t ticket, int timeout_ms, jpsi_status *result,
+                            double *latency_s);
+jpsi_status jpsi_serve_stop(jpsi_ctx *ctx);
+
+/* Device-time accounting of runs, for roofline measurements.  While enabled,
+ * each run records CUDA events on its stream around its phases: the
+ * warp-per-event counting kernel (light_ms), the rest of the counting phase
+ * (block-per-event kernel, accept bits, scan: count_rest_ms) and the
+ * triplet-writing phase (emit_ms).  Enabling resets the totals. */
+typedef struct {
+    int64_t runs;
+    int64_t kernel_launches; /* kernels of this library launched by those runs */
+    double light_ms, count_rest_ms, emit_ms;
+} jpsi_timing;
+jpsi_status jpsi_timing_enable(jpsi_ctx *ctx, int enable);
+jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);
+
+/* Static description of a status code. */
+const char *jpsi_strerror(jpsi_status status);
+
+/* Detail of the last error seen on this context (empty if none). */
+const char *jpsi_last_error(const jpsi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JPSI_H */

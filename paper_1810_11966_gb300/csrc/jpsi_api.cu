@@ -1,0 +1,792 @@
+// C-ABI of libjpsi (include/jpsi.h): contexts, scratch management, the
+// plain and batched run forms, host-buffer runs, the autotuner and the
+// continuous-batching serving loop.  All device work is in jpsi_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/jpsi.h"
+#include "jpsi_internal.h"
+
+using namespace jpsi;
+
+namespace {
+
+constexpr size_t kDefaultBudget = (size_t)8 << 30;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-run device state: job descriptor, control block, graphs.  The serving
+// loop owns one per slot; plain runs use the context's own.
+struct RunState {
+    Job* d_job = nullptr;
+    Job* h_job = nullptr;     // pinned
+    Ctrl* d_ctrl = nullptr;
+    Ctrl* h_ctrl = nullptr;   // pinned
+    DevBuf unit_counts, track_counts, ev_class, glist, block_sums, trip_off;
+    cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr;
+    int g_cfg_id = -1;
+    cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
+};
+
+struct Slot {
+    RunState rs;
+    DevBuf x, y, z, off, accept, tracks, trip_off, triplets;
+    int64_t cap_events = 0, cap_hits = 0, cap_trip = 0;
+    cudaStream_t stream = nullptr;
+    // current request
+    jpsi_batch batch{};
+    jpsi_outputs* out = nullptr;
+    uint64_t ticket = 0;
+    std::chrono::steady_clock::time_point t_submit;
+    bool busy = false;
+};
+
+struct Done {
+    jpsi_status st;
+    double latency;
+};
+
+}  // namespace
+
+struct jpsi_ctx {
+    jpsi_params p{};
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    int n_sm = 0;
+    bool pageable_ok = false;
+    float cx = 0, cy = 0, K = 0;
+    LaunchCfg plain_cfg, batch_cfg;
+    int grab = 2;
+    int cfg_id = 0;  // bumps when the launch shape changes (graphs re-captured)
+    cudaStream_t cap_stream = nullptr;
+    RunState rs;
+    // device copies for jpsi_run_host
+    DevBuf hx, hy, hz, hoff, hacc, htc, htoff, htrip;
+    std::string last_error;
+    std::mutex err_mu, cap_mu, alloc_mu;
+    std::atomic<bool> timing{false};
+    jpsi_timing tm{};
+    std::atomic<bool> busy{false};
+    // serving
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<Slot*> slots;
+    std::vector<std::thread> workers;
+    std::deque<int> free_slots;
+    std::map<uint64_t, Done> done;
+    uint64_t next_ticket = 1;
+    bool serving = false, stopping = false;
+    std::vector<std::condition_variable*> slot_cv;
+};
+
+namespace {
+
+struct BusyGuard {
+    jpsi_ctx* c;
+    bool ok;
+    explicit BusyGuard(jpsi_ctx* ctx) : c(ctx) {
+        bool expected = false;
+        ok = c->busy.compare_exchange_strong(expected, true);
+    }
+    ~BusyGuard() {
+        if (ok) c->busy.store(false);
+    }
+};
+
+jpsi_status fail(jpsi_ctx* c, jpsi_status st, const std::string& msg) {
+    if (c) {
+        std::lock_guard<std::mutex> lk(c->err_mu);
+        c->last_error = msg;
+    }
+    return st;
+}
+
+jpsi_status cuda_fail(jpsi_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, JPSI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Grows a device buffer within the context budget (contents not kept).
+jpsi_status ensure(jpsi_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+    if (bytes <= b.bytes) return JPSI_OK;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
+    const size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
+    const size_t extra = nb - b.bytes;
+    if (c->used + extra > c->budget)
+        return fail(c, JPSI_ENOMEM, std::string("scratch for ") + what + " exceeds the device budget");
+    void* p = nullptr;
+    if (cudaMalloc(&p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, JPSI_ENOMEM, std::string("cudaMalloc failed for ") + what);
+    }
+    if (b.p) cudaFree(b.p);
+    c->used = c->used - b.bytes + nb;
+    b.p = p;
+    b.bytes = nb;
+    return JPSI_OK;
+}
+
+void release(jpsi_ctx* c, DevBuf& b) {
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
+    if (b.p) cudaFree(b.p);
+    c->used -= b.bytes;
+    b = DevBuf{};
+}
+
+jpsi_status params_ok(const jpsi_params* p) {
+    if (!p) return JPSI_EINVAL;
+    if (p->n_stations < 1 || p->n_stations > kMaxStations) return JPSI_EINVAL;
+    if (p->trigger_station < 0 || p->trigger_station >= p->n_stations) return JPSI_EINVAL;
+    if (p->mode != JPSI_MODE_PAPER && p->mode != JPSI_MODE_CHAIN) return JPSI_EINVAL;
+    if (p->ndf < 1 || p->min_candidates < 0) return JPSI_EINVAL;
+    if (!(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) || std::isinf(p->t_xz) || std::isinf(p->t_yz)) return JPSI_EINVAL;
+    return JPSI_OK;
+}
+
+// Pruning factor: sqrt(max C) (1 + 1e-4) + 1e-20, rounded up to float.
+float pruning_K(float cx, float cy) {
+    const double k = std::sqrt((double)std::max(cx, cy)) * (1.0 + 1e-4) + 1e-20;
+    float f = (float)k;
+    if ((double)f < k) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+bool device_accessible(jpsi_ctx* c, const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return c->pageable_ok;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == c->device;
+    if (a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost) return true;
+    return c->pageable_ok;
+}
+
+jpsi_status check_batch(jpsi_ctx* c, const jpsi_batch* b, const jpsi_outputs* o, bool device_ptrs) {
+    if (!b || !o) return fail(c, JPSI_EINVAL, "null batch or outputs");
+    const int64_t S = c->p.n_stations;
+    if (b->n_events < 0 || b->n_hits < 0) return fail(c, JPSI_EINVAL, "negative sizes");
+    if (b->n_hits >= ((int64_t)1 << 31)) return fail(c, JPSI_EINVAL, "n_hits must be < 2^31");
+    if (b->n_events > (((int64_t)1 << 31) - 2) / (3 * S)) return fail(c, JPSI_EINVAL, "too many events for int32 offsets");
+    if (b->n_events == 0 && b->n_hits != 0) return fail(c, JPSI_EINVAL, "hits without events");
+    if (b->n_events > 0 && !b->offsets) return fail(c, JPSI_EINVAL, "offsets missing");
+    if (b->n_hits > 0 && (!b->x || !b->y || !b->z)) return fail(c, JPSI_EINVAL, "hit arrays missing");
+    if (o->triplets && !o->trip_off) return fail(c, JPSI_EINVAL, "triplets need trip_off");
+    if (o->trip_capacity < 0) return fail(c, JPSI_EINVAL, "negative triplet capacity");
+    if (device_ptrs) {
+        const void* ptrs[] = {b->x, b->y, b->z, b->offsets, o->accept_bits, o->track_counts, o->trip_off, o->triplets};
+        for (const void* p : ptrs)
+            if (!device_accessible(c, p)) return fail(c, JPSI_EINVAL, "pointer is not device-accessible");
+    }
+    return JPSI_OK;
+}
+
+// Prepares scratch and the job descriptor of a run.
+jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o) {
+    const int64_t S = c->p.n_stations;
+    const int64_t ne = b->n_events, nu = ne * S;
+    jpsi_status st;
+    if ((st = ensure(c, rs.unit_counts, (size_t)std::max<int64_t>(nu, 1) * 4, "unit counts")) != JPSI_OK) return st;
+    if ((st = ensure(c, rs.ev_class, (size_t)std::max<int64_t>(ne, 1), "event classes")) != JPSI_OK) return st;
+    if ((st = ensure(c, rs.glist, (size_t)std::max<int64_t>(ne, 1) * 4, "event list")) != JPSI_OK) return st;
+    const int64_t ntiles = (nu + 4095) / 4096 + 1;
+    if ((st = ensure(c, rs.block_sums, (size_t)ntiles * 8, "scan")) != JPSI_OK) return st;
+    if (!o->track_counts && (st = ensure(c, rs.track_counts, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts")))
+        return st;
+    if (!o->trip_off && (st = ensure(c, rs.trip_off, (size_t)(nu + 1) * 8, "triplet offsets"))) return st;
+    Job& j = *rs.h_job;
+    j.x = b->x;
+    j.y = b->y;
+    j.z = b->z;
+    j.off = b->offsets;
+    j.n_events = ne;
+    j.n_hits = b->n_hits;
+    j.S = c->p.n_stations;
+    j.trig = c->p.trigger_station;
+    j.mode = c->p.mode;
+    j.minc = c->p.min_candidates;
+    j.cx = c->cx;
+    j.cy = c->cy;
+    j.K = c->K;
+    j.grab = c->grab;
+    j.unit_counts = (int32_t*)rs.unit_counts.p;
+    j.track_counts = o->track_counts ? o->track_counts : (int32_t*)rs.track_counts.p;
+    j.ev_class = (uint8_t*)rs.ev_class.p;
+    j.glist = (int32_t*)rs.glist.p;
+    j.accept_bits = o->accept_bits;
+    j.trip_off = o->trip_off ? o->trip_off : (int64_t*)rs.trip_off.p;
+    j.block_sums = (int64_t*)rs.block_sums.p;
+    j.triplets = o->triplets;
+    j.ctrl = rs.d_ctrl;
+    return JPSI_OK;
+}
+
+jpsi_status state_init(jpsi_ctx* c, RunState& rs) {
+    if (cudaMalloc(&rs.d_job, sizeof(Job)) != cudaSuccess || cudaMalloc(&rs.d_ctrl, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMallocHost(&rs.h_job, sizeof(Job)) != cudaSuccess || cudaMallocHost(&rs.h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, JPSI_ENOMEM, "control block allocation failed");
+    }
+    memset(rs.h_job, 0, sizeof(Job));
+    memset(rs.h_ctrl, 0, sizeof(Ctrl));
+    for (cudaEvent_t& e : rs.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(c, JPSI_ECUDA, "event creation failed");
+    return JPSI_OK;
+}
+
+void destroy_graphs(RunState& rs) {
+    cudaGraphExec_t* gs[] = {&rs.g_light, &rs.g_rest, &rs.g_emit};
+    for (cudaGraphExec_t* g : gs) {
+        if (*g) cudaGraphExecDestroy(*g);
+        *g = nullptr;
+    }
+}
+
+void state_free(jpsi_ctx* c, RunState& rs) {
+    destroy_graphs(rs);
+    for (cudaEvent_t& e : rs.ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (rs.d_job) cudaFree(rs.d_job);
+    if (rs.d_ctrl) cudaFree(rs.d_ctrl);
+    if (rs.h_job) cudaFreeHost(rs.h_job);
+    if (rs.h_ctrl) cudaFreeHost(rs.h_ctrl);
+    rs.d_job = nullptr;
+    rs.d_ctrl = nullptr;
+    rs.h_job = nullptr;
+    rs.h_ctrl = nullptr;
+    release(c, rs.unit_counts);
+    release(c, rs.track_counts);
+    release(c, rs.ev_class);
+    release(c, rs.glist);
+    release(c, rs.block_sums);
+    release(c, rs.trip_off);
+}
+
+// Captures the count and emit phases of the batched form into graphs that
+// read their job from rs.d_job (valid for every batch).
+jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
+    if (rs.g_light && rs.g_cfg_id == c->cfg_id) return JPSI_OK;
+    std::lock_guard<std::mutex> cap_lock(c->cap_mu);
+    destroy_graphs(rs);
+    for (int phase = 0; phase < 3; ++phase) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+        cudaError_t le = phase == 0   ? launch_light_count(rs.d_job, 0, c->batch_cfg, true, c->cap_stream)
+                         : phase == 1 ? launch_count_rest(rs.d_job, c->batch_cfg, c->cap_stream)
+                                      : launch_emit_phase(rs.d_job, 0, c->batch_cfg, true, c->cap_stream);
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(c, le, "graph capture launch");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph end capture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        (phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : rs.g_emit) = ge;
+    }
+    rs.g_cfg_id = c->cfg_id;
+    return JPSI_OK;
+}
+
+// Accumulates per-phase device times of a finished run (events already complete).
+void add_timing(jpsi_ctx* c, RunState& rs, int launches, bool emitted) {
+    if (!c->timing.load()) return;
+    float a = 0, b = 0, d = 0;
+    cudaEventElapsedTime(&a, rs.ev[0], rs.ev[1]);
+    cudaEventElapsedTime(&b, rs.ev[1], rs.ev[2]);
+    if (emitted) cudaEventElapsedTime(&d, rs.ev[3], rs.ev[4]);
+    std::lock_guard<std::mutex> lk(c->err_mu);
+    c->tm.runs += 1;
+    c->tm.kernel_launches += launches;
+    c->tm.light_ms += a;
+    c->tm.count_rest_ms += b;
+    c->tm.emit_ms += d;
+}
+
+// The common run: count phase, status/capacity check, emit phase.
+jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, cudaStream_t st,
+                       bool batched) {
+    jpsi_status s;
+    if ((s = prepare(c, rs, b, o)) != JPSI_OK) return s;
+    const int64_t ne = b->n_events, nu = ne * c->p.n_stations;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(rs.d_job, rs.h_job, sizeof(Job), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "job upload");
+    if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
+    const bool timing = c->timing.load();
+    if (batched && (s = capture_graphs(c, rs)) != JPSI_OK) return s;
+    if (timing) cudaEventRecord(rs.ev[0], st);
+    e = batched ? cudaGraphLaunch(rs.g_light, st) : launch_light_count(rs.d_job, ne, c->plain_cfg, false, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "light count");
+    if (timing) cudaEventRecord(rs.ev[1], st);
+    e = batched ? cudaGraphLaunch(rs.g_rest, st) : launch_count_rest(rs.d_job, c->plain_cfg, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "count rest");
+    if (timing) cudaEventRecord(rs.ev[2], st);
+    int launches = kLaunchesLight + kLaunchesRest;
+    (void)nu;
+    if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "ctrl readback");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "count phase");
+    const Ctrl ctl = *rs.h_ctrl;
+    if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
+    o->trip_needed = ctl.trip_total;
+    if (!o->triplets) {
+        add_timing(c, rs, launches, false);
+        return JPSI_OK;
+    }
+    if (ctl.trip_total > o->trip_capacity)
+        return fail(c, JPSI_ECAPACITY, "triplet capacity " + std::to_string(o->trip_capacity) + " < needed " +
+                                           std::to_string(ctl.trip_total));
+    if (ctl.trip_total == 0) {
+        add_timing(c, rs, launches, false);
+        return JPSI_OK;
+    }
+    if (timing) cudaEventRecord(rs.ev[3], st);
+    e = batched ? cudaGraphLaunch(rs.g_emit, st) : launch_emit_phase(rs.d_job, ne, c->plain_cfg, false, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "emit");
+    if (timing) cudaEventRecord(rs.ev[4], st);
+    launches += kLaunchesEmit;
+    if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "ctrl readback");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "emit phase");
+    if (rs.h_ctrl->status & kStEmitMismatch) return fail(c, JPSI_ECUDA, "internal: emit pass count mismatch");
+    add_timing(c, rs, launches, true);
+    return JPSI_OK;
+}
+
+void set_launch_shape(jpsi_ctx* c, int wpb, int grab) {
+    c->grab = grab;
+    const int lb = std::max(1, light_max_blocks_per_sm(wpb));
+    const int gb = std::max(1, generic_max_blocks_per_sm(256));
+    c->batch_cfg.light_wpb = wpb;
+    c->batch_cfg.light_blocks = c->n_sm * lb;
+    c->batch_cfg.generic_threads = 256;
+    c->batch_cfg.generic_blocks = c->n_sm * gb;
+    c->batch_cfg.scan_blocks = c->n_sm * 2;
+    c->plain_cfg = c->batch_cfg;
+    c->plain_cfg.light_wpb = 4;
+    c->plain_cfg.light_blocks = 0;
+    ++c->cfg_id;
+}
+
+// Copies H2D of a host batch into device buffers `x, y, z, off`.
+jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevBuf& z, DevBuf& off,
+                   jpsi_batch* db, cudaStream_t st) {
+    const int64_t S = c->p.n_stations;
+    const size_t hb_bytes = (size_t)hb->n_hits * 4;
+    const size_t ob = (size_t)(hb->n_events * 3 * S + 1) * 4;
+    jpsi_status s;
+    if ((s = ensure(c, x, std::max<size_t>(hb_bytes, 4), "hits x")) || (s = ensure(c, y, std::max<size_t>(hb_bytes, 4), "hits y")) ||
+        (s = ensure(c, z, std::max<size_t>(hb_bytes, 4), "hits z")) || (s = ensure(c, off, ob, "offsets")))
+        return s;
+    cudaError_t e = cudaSuccess;
+    if (hb_bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(x.p, hb->x, hb_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(y.p, hb->y, hb_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(z.p, hb->z, hb_bytes, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && hb->n_events > 0) e = cudaMemcpyAsync(off.p, hb->offsets, ob, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "input upload");
+    *db = *hb;
+    db->x = (const float*)x.p;
+    db->y = (const float*)y.p;
+    db->z = (const float*)z.p;
+    db->offsets = (const int32_t*)off.p;
+    return JPSI_OK;
+}
+
+// jpsi_run on host buffers with the given device buffers.
+jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_outputs* ho, DevBuf& x, DevBuf& y,
+                          DevBuf& z, DevBuf& off, DevBuf& acc, DevBuf& tc, DevBuf& toff, DevBuf& trip,
+                          int64_t trip_cap_dev, cudaStream_t st) {
+    jpsi_batch db;
+    jpsi_status s = upload(c, hb, x, y, z, off, &db, st);
+    if (s != JPSI_OK) return s;
+    const int64_t ne = hb->n_events, nu = ne * c->p.n_stations;
+    jpsi_outputs dout{};
+    if (ho->accept_bits) {
+        if ((s = ensure(c, acc, (size_t)std::max<int64_t>((ne + 31) / 32, 1) * 4, "accept bits"))) return s;
+        dout.accept_bits = (uint32_t*)acc.p;
+    }
+    if (ho->track_counts) {
+        if ((s = ensure(c, tc, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts"))) return s;
+        dout.track_counts = (int32_t*)tc.p;
+    }
+    if (ho->trip_off || ho->triplets) {
+        if ((s = ensure(c, toff, (size_t)(nu + 1) * 8, "triplet offsets"))) return s;
+        dout.trip_off = (int64_t*)toff.p;
+    }
+    if (ho->triplets) {
+        const int64_t cap = trip_cap_dev >= 0 ? std::min(trip_cap_dev, ho->trip_capacity) : ho->trip_capacity;
+        if ((s = ensure(c, trip, (size_t)std::max<int64_t>(cap, 1) * 12, "triplets"))) return s;
+        dout.triplets = (int32_t*)trip.p;
+        dout.trip_capacity = cap;
+    }
+    s = run_device(c, rs, &db, &dout, st, true);
+    ho->trip_needed = dout.trip_needed;
+    if (s != JPSI_OK && s != JPSI_ECAPACITY) return s;
+    cudaError_t e = cudaSuccess;
+    if (ho->accept_bits && ne > 0)
+        e = cudaMemcpyAsync(ho->accept_bits, acc.p, (size_t)((ne + 31) / 32) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->track_counts && ne > 0)
+        e = cudaMemcpyAsync(ho->track_counts, tc.p, (size_t)ne * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->trip_off)
+        e = cudaMemcpyAsync(ho->trip_off, toff.p, (size_t)(nu + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->triplets && s == JPSI_OK && dout.trip_needed > 0)
+        e = cudaMemcpyAsync(ho->triplets, trip.p, (size_t)dout.trip_needed * 12, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output download");
+    return s;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* jpsi_strerror(jpsi_status s) {
+    switch (s) {
+        case JPSI_OK: return "ok";
+        case JPSI_EINVAL: return "invalid argument or input";
+        case JPSI_ENOMEM: return "out of memory or over the device budget";
+        case JPSI_ECAPACITY: return "triplet buffer too small";
+        case JPSI_ECUDA: return "CUDA error";
+        case JPSI_ETIMEOUT: return "timed out";
+        case JPSI_EBUSY: return "context busy";
+    }
+    return "unknown status";
+}
+
+const char* jpsi_last_error(const jpsi_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+
+jpsi_status jpsi_create(const jpsi_params* params, int device, size_t hbm_budget, jpsi_ctx** out) {
+    if (!out) return JPSI_EINVAL;
+    *out = nullptr;
+    if (params_ok(params) != JPSI_OK) return JPSI_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? JPSI_ECUDA : JPSI_EINVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return JPSI_ECUDA;
+    jpsi_ctx* c = new (std::nothrow) jpsi_ctx;
+    if (!c) return JPSI_ENOMEM;
+    c->p = *params;
+    c->device = device;
+    c->budget = hbm_budget ? hbm_budget : kDefaultBudget;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    int pma = 0;
+    cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device);
+    c->pageable_ok = pma != 0;
+    c->cx = (float)params->ndf * params->t_xz;
+    c->cy = (float)params->ndf * params->t_yz;
+    c->K = pruning_K(c->cx, c->cy);
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return JPSI_ECUDA;
+    }
+    if (state_init(c, c->rs) != JPSI_OK) {
+        jpsi_destroy(c);
+        return JPSI_ENOMEM;
+    }
+    set_launch_shape(c, 4, 2);
+    *out = c;
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_serve_stop(jpsi_ctx* c);
+
+void jpsi_destroy(jpsi_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    jpsi_serve_stop(c);
+    cudaDeviceSynchronize();
+    state_free(c, c->rs);
+    DevBuf* bufs[] = {&c->hx, &c->hy, &c->hz, &c->hoff, &c->hacc, &c->htc, &c->htoff, &c->htrip};
+    for (DevBuf* b : bufs) release(c, *b);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+jpsi_status jpsi_run_plain(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    jpsi_status s = check_batch(c, b, o, true);
+    if (s != JPSI_OK) return s;
+    return run_device(c, c->rs, b, o, (cudaStream_t)stream, false);
+}
+
+jpsi_status jpsi_run(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    jpsi_status s = check_batch(c, b, o, true);
+    if (s != JPSI_OK) return s;
+    return run_device(c, c->rs, b, o, (cudaStream_t)stream, true);
+}
+
+jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    jpsi_status s = check_batch(c, b, o, false);
+    if (s != JPSI_OK) return s;
+    return run_host_with(c, c->rs, b, o, c->hx, c->hy, c->hz, c->hoff, c->hacc, c->htc, c->htoff, c->htrip, -1,
+                         (cudaStream_t)stream);
+}
+
+jpsi_status jpsi_timing_enable(jpsi_ctx* c, int enable) {
+    if (!c) return JPSI_EINVAL;
+    std::lock_guard<std::mutex> lk(c->err_mu);
+    c->tm = jpsi_timing{};
+    c->timing.store(enable != 0);
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_timing_get(jpsi_ctx* c, jpsi_timing* out) {
+    if (!c || !out) return JPSI_EINVAL;
+    std::lock_guard<std::mutex> lk(c->err_mu);
+    *out = c->tm;
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_autotune(jpsi_ctx* c, const jpsi_batch* sample) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    jpsi_outputs o{};
+    jpsi_status s = check_batch(c, sample, &o, true);
+    if (s != JPSI_OK) return s;
+    DevBuf acc;
+    if ((s = ensure(c, acc, (size_t)std::max<int64_t>((sample->n_events + 31) / 32, 1) * 4, "autotune"))) return s;
+    o.accept_bits = (uint32_t*)acc.p;
+    cudaStream_t st = c->cap_stream;
+    const int wpbs[] = {2, 4, 8};
+    const int grabs[] = {1, 2, 4, 8};
+    float best = INFINITY;
+    int bw = 4, bg = 2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int w : wpbs) {
+        if (light_max_blocks_per_sm(w) < 1) continue;
+        for (int gr : grabs) {
+            set_launch_shape(c, w, gr);
+            float tot = 0;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                cudaEventRecord(e0, st);
+                ok = run_device(c, c->rs, sample, &o, st, true) == JPSI_OK;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;  // first run warms up / captures
+            }
+            if (ok && tot < best) {
+                best = tot;
+                bw = w;
+                bg = gr;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release(c, acc);
+    set_launch_shape(c, bw, bg);
+    return JPSI_OK;
+}
+
+// ------------------------------------------------------------- serving
+
+static void slot_worker(jpsi_ctx* c, int si) {
+    cudaSetDevice(c->device);
+    Slot* sl = c->slots[si];
+    std::unique_lock<std::mutex> lk(c->mu);
+    for (;;) {
+        c->slot_cv[si]->wait(lk, [&] { return c->stopping || sl->busy; });
+        if (!sl->busy && c->stopping) return;
+        jpsi_batch b = sl->batch;
+        jpsi_outputs* o = sl->out;
+        lk.unlock();
+        jpsi_status s = run_host_with(c, sl->rs, &b, o, sl->x, sl->y, sl->z, sl->off, sl->accept, sl->tracks,
+                                      sl->trip_off, sl->triplets, sl->cap_trip, sl->stream);
+        const double lat =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - sl->t_submit).count();
+        lk.lock();
+        c->done[sl->ticket] = Done{s, lat};
+        sl->busy = false;
+        c->free_slots.push_back(si);
+        c->cv.notify_all();
+    }
+}
+
+jpsi_status jpsi_serve_start(jpsi_ctx* c, int n_slots, int64_t slot_events, int64_t slot_hits,
+                             int64_t slot_triplets) {
+    if (!c || n_slots < 1 || n_slots > 64 || slot_events < 0 || slot_hits < 0 || slot_triplets < 0)
+        return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    if (c->serving) return fail(c, JPSI_EINVAL, "serving already started");
+    if (slot_hits >= ((int64_t)1 << 31)) return fail(c, JPSI_EINVAL, "slot_hits must be < 2^31");
+    const int64_t S = c->p.n_stations;
+    jpsi_status s = JPSI_OK;
+    for (int i = 0; i < n_slots && s == JPSI_OK; ++i) {
+        Slot* sl = new Slot;
+        c->slots.push_back(sl);
+        c->slot_cv.push_back(new std::condition_variable);
+        sl->cap_events = slot_events;
+        sl->cap_hits = slot_hits;
+        sl->cap_trip = slot_triplets;
+        if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            s = fail(c, JPSI_ECUDA, "stream creation");
+            break;
+        }
+        if ((s = state_init(c, sl->rs)) != JPSI_OK) break;
+        const int64_t ne = std::max<int64_t>(slot_events, 1), nu = ne * S;
+        const size_t hb = (size_t)std::max<int64_t>(slot_hits, 1) * 4;
+        // reserve everything up front: admission is by free slots within the budget
+        if ((s = ensure(c, sl->x, hb, "slot hits")) || (s = ensure(c, sl->y, hb, "slot hits")) ||
+            (s = ensure(c, sl->z, hb, "slot hits")) || (s = ensure(c, sl->off, (size_t)(ne * 3 * S + 1) * 4, "slot offsets")) ||
+            (s = ensure(c, sl->accept, (size_t)((ne + 31) / 32) * 4, "slot accept")) ||
+            (s = ensure(c, sl->tracks, (size_t)ne * 4, "slot tracks")) ||
+            (s = ensure(c, sl->trip_off, (size_t)(nu + 1) * 8, "slot trip_off")) ||
+            (s = ensure(c, sl->triplets, (size_t)std::max<int64_t>(slot_triplets, 1) * 12, "slot triplets")) ||
+            (s = ensure(c, sl->rs.unit_counts, (size_t)nu * 4, "slot unit counts")) ||
+            (s = ensure(c, sl->rs.ev_class, (size_t)ne, "slot classes")) ||
+            (s = ensure(c, sl->rs.track_counts, (size_t)ne * 4, "slot track scratch")) ||
+            (s = ensure(c, sl->rs.trip_off, (size_t)(nu + 1) * 8, "slot offsets scratch")) ||
+            (s = ensure(c, sl->rs.glist, (size_t)ne * 4, "slot list")) ||
+            (s = ensure(c, sl->rs.block_sums, (size_t)((nu + 4095) / 4096 + 1) * 8, "slot scan")))
+            break;
+        // graphs are captured with the context's launch shape
+        if ((s = capture_graphs(c, sl->rs)) != JPSI_OK) break;
+        c->free_slots.push_back(i);
+    }
+    if (s != JPSI_OK) {
+        c->serving = true;  // let stop() tear down what exists
+        jpsi_serve_stop(c);
+        return s;
+    }
+    c->stopping = false;
+    c->serving = true;
+    for (int i = 0; i < n_slots; ++i) c->workers.emplace_back(slot_worker, c, i);
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_serve_submit(jpsi_ctx* c, const jpsi_batch* hb, jpsi_outputs* ho, uint64_t* ticket) {
+    if (!c || !hb || !ho || !ticket) return JPSI_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (!c->serving || c->stopping) return JPSI_EINVAL;
+    if (hb->n_events < 0 || hb->n_hits < 0 || (hb->n_events > 0 && !hb->offsets) ||
+        (hb->n_hits > 0 && (!hb->x || !hb->y || !hb->z)) || (ho->triplets && !ho->trip_off))
+        return JPSI_EINVAL;
+    const Slot* s0 = c->slots[0];
+    if (hb->n_events > s0->cap_events || hb->n_hits > s0->cap_hits) return JPSI_EINVAL;
+    // back-pressure: block until a slot frees up
+    c->cv.wait(lk, [&] { return !c->free_slots.empty() || c->stopping; });
+    if (c->stopping) return JPSI_EINVAL;
+    const int si = c->free_slots.front();
+    c->free_slots.pop_front();
+    Slot* sl = c->slots[si];
+    sl->batch = *hb;
+    sl->out = ho;
+    sl->ticket = c->next_ticket++;
+    sl->t_submit = t0;
+    sl->busy = true;
+    *ticket = sl->ticket;
+    c->slot_cv[si]->notify_one();
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_serve_wait(jpsi_ctx* c, uint64_t ticket, int timeout_ms, jpsi_status* result, double* latency_s) {
+    if (!c) return JPSI_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto ready = [&] { return c->done.count(ticket) != 0; };
+    if (timeout_ms < 0)
+        c->cv.wait(lk, ready);
+    else if (!c->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return JPSI_ETIMEOUT;
+    const Done d = c->done[ticket];
+    c->done.erase(ticket);
+    if (result) *result = d.st;
+    if (latency_s) *latency_s = d.latency;
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_serve_stop(jpsi_ctx* c) {
+    if (!c) return JPSI_EINVAL;
+    {
+        std::unique_lock<std::mutex> lk(c->mu);
+        if (!c->serving) return JPSI_OK;
+        // finish what was admitted
+        c->cv.wait(lk, [&] {
+            for (Slot* s : c->slots)
+                if (s->busy) return false;
+            return true;
+        });
+        c->stopping = true;
+        for (auto* cv : c->slot_cv) cv->notify_all();
+        c->cv.notify_all();
+    }
+    for (auto& t : c->workers) t.join();
+    c->workers.clear();
+    for (Slot* sl : c->slots) {
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        state_free(c, sl->rs);
+        DevBuf* bufs[] = {&sl->x, &sl->y, &sl->z, &sl->off, &sl->accept, &sl->tracks, &sl->trip_off, &sl->triplets};
+        for (DevBuf* b : bufs) release(c, *b);
+        if (sl->stream) cudaStreamDestroy(sl->stream);
+        delete sl;
+    }
+    c->slots.clear();
+    for (auto* cv : c->slot_cv) delete cv;
+    c->slot_cv.clear();
+    c->free_slots.clear();
+    c->done.clear();
+    c->serving = false;
+    c->stopping = false;
+    return JPSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Device-side arithmetic of the J/psi triplet selection (arXiv:1810.11966,
+// Sec. 3.2) and the conservative pruning it runs behind.
+//
+// Exact part (decides results): P1, the fit of a triplet with the vertex by
+// u = m z in both planes and the cut on the summed squared residual, and P2,
+// the CHAIN-mode compatibility of a station triplet with a trigger slope.
+// Both use __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn so that nothing is
+// contracted into an FMA and every step rounds to nearest in the order below.
+//
+// Pruning part (only skips work): per hit, s_u = u * fl(1/z) and a bound
+//     b = K * fl(1/z) + kappa * (|s_x| + |s_y|) + tau,
+//     K = sqrt(max C)(1 + 1e-4) + 1e-20 (rounded up), kappa = 2^-20, tau = 1e-37.
+// If a triplet passes P1 with slope m, each hit obeys
+//     |u_k/z_k - m| <= (|r_k|(1+2eps) + eps |m z_k|) / z_k,  |r_k| <= sqrt(C)(1+2eps) + 2^-74
+// (eps = 2^-24; the 2^-74 covers squares that underflow).  Subtracting the
+// relations of two hits and adding the rounding of s (<= 2.0001 eps |s|) gives
+//     |s_i - s_j| <= b_i (1 - 5e-5) + b_j (1 - 5e-5),
+// so the FP32 test |fl(s_i - s_j)| <= fl(b_i + b_j) never rejects a pair that
+// belongs to a passing triplet.  Hits with a non-finite coordinate cannot pass
+// P1 at all (Szz, Suz or a residual becomes Inf/NaN) and are dropped; hits with
+// finite coordinates but a non-finite s or b send their event to the
+// unpruned path.
+#pragma once
+#include <cstdint>
+
+namespace jpsi {
+
+constexpr float kKappa = 9.5367431640625e-07f;  // 2^-20
+constexpr float kTau = 1e-37f;
+constexpr int kNB = 32;                          // slope bins per layer
+
+struct Cuts {
+    float cx, cy;  // thresholds on S_x, S_y: fl32(ndf * t)
+    float K;       // pruning slope factor (see above)
+};
+
+// ---------------------------------------------------------------- P1 / P2
+
+// Szz = (z0*z0 + z1*z1) + z2*z2
+__device__ __forceinline__ float sum_sq3(float a, float b, float c) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+}
+
+// (u0*z0 + u1*z1) + u2*z2
+__device__ __forceinline__ float dot3(float u0, float u1, float u2, float z0, float z1, float z2) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(u0, z0), __fmul_rn(u1, z1)), __fmul_rn(u2, z2));
+}
+
+// (r0*r0 + r1*r1) + r2*r2 with r_k = u_k - m*z_k
+__device__ __forceinline__ float resid3(float u0, float u1, float u2, float z0, float z1, float z2, float m) {
+    const float r0 = __fsub_rn(u0, __fmul_rn(m, z0));
+    const float r1 = __fsub_rn(u1, __fmul_rn(m, z1));
+    const float r2 = __fsub_rn(u2, __fmul_rn(m, z2));
+    return sum_sq3(r0, r1, r2);
+}
+
+// P1: Sec. 3.2 step 2 on hits k = 0,1,2 of layers 0,1,2.
+__device__ __forceinline__ bool fit_pass(const float x[3], const float y[3], const float z[3], const Cuts& c,
+                                         float& mx, float& my) {
+    const float szz = sum_sq3(z[0], z[1], z[2]);
+    mx = __fdiv_rn(dot3(x[0], x[1], x[2], z[0], z[1], z[2]), szz);
+    my = __fdiv_rn(dot3(y[0], y[1], y[2], z[0], z[1], z[2]), szz);
+    const float sx = resid3(x[0], x[1], x[2], z[0], z[1], z[2], mx);
+    const float sy = resid3(y[0], y[1], y[2], z[0], z[1], z[2], my);
+    return (sx <= c.cx) && (sy <= c.cy);  // ordered: NaN fails
+}
+
+// P2: residuals of a station triplet against a trigger slope, no refit.
+__device__ __forceinline__ bool chain_pass(const float x[3], const float y[3], const float z[3], float mx, float my,
+                                           const Cuts& c) {
+    return (resid3(x[0], x[1], x[2], z[0], z[1], z[2], mx) <= c.cx) &&
+           (resid3(y[0], y[1], y[2], z[0], z[1], z[2], my) <= c.cy);
+}
+
+// Necessary condition of P2 for one hit: S >= fl(r_k^2) for every k because
+// the partial sums of non-negative terms never round below a term.
+__device__ __forceinline__ bool tube_pass(float x, float y, float z, float mx, float my, const Cuts& c) {
+    const float rx = __fsub_rn(x, __fmul_rn(mx, z));
+    const float ry = __fsub_rn(y, __fmul_rn(my, z));
+    return (__fmul_rn(rx, rx) <= c.cx) && (__fmul_rn(ry, ry) <= c.cy);
+}
+
+// ------------------------------------------------------------- pruning
+
+struct HitPrep {
+    float sx, sy, b;
+    bool live;  // all coordinates finite (else the hit can never pass)
+    bool wild;  // live but s or b not finite: no pruning for its event
+    bool zbad;  // z <= 0: invalid input
+};
+
+__device__ __forceinline__ HitPrep hit_prep(float x, float y, float z, float K) {
+    HitPrep h;
+    h.zbad = z <= 0.0f;
+    h.live = isfinite(x) && isfinite(y) && isfinite(z);
+    const float iz = __frcp_rn(z);
+    h.sx = __fmul_rn(x, iz);
+    h.sy = __fmul_rn(y, iz);
+    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, __fadd_rn(fabsf(h.sx), fabsf(h.sy)))), kTau);
+    h.wild = h.live && !(isfinite(h.sx) && isfinite(h.sy) && isfinite(h.b));
+    return h;
+}
+
+// May hits i and j belong to one passing triplet?  (never false for such a pair)
+__device__ __forceinline__ bool pair_ok(float sxi, float syi, float bi, float sxj, float syj, float bj) {
+    const float bb = __fadd_rn(bi, bj);
+    return (fabsf(__fsub_rn(sxi, sxj)) <= bb) && (fabsf(__fsub_rn(syi, syj)) <= bb);
+}
+
+// May a hit pass the tube of trigger slope (mx, my)?  From tube_pass:
+// |s - m| <= b (1 - 5e-5) + 2^-21 |m| for a passing hit.
+__device__ __forceinline__ bool tube_ok(float sx, float sy, float b, float mx, float my) {
+    const float wx = __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx)));
+    const float wy = __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my)));
+    return (fabsf(__fsub_rn(sx, mx)) <= wx) && (fabsf(__fsub_rn(sy, my)) <= wy);
+}
+
+// Slope bins of one layer: bin(v) = clamp(floor((v - lo) * inv_w), 0, NB-1),
+// non-decreasing in v (each step is a monotone rounding), so a value range
+// maps to a contiguous bin range.
+__device__ __forceinline__ int slope_bin(float v, float lo, float inv_w) {
+    const float t = floorf(__fmul_rn(__fsub_rn(v, lo), inv_w));
+    return (int)fminf(fmaxf(t, 0.0f), (float)(kNB - 1));  // NaN -> 0 (only when inv_w = 0)
+}
+
+// Bins that contain every stored value v with |v - c| <= W (1 + 2^-20):
+// the half-width is padded by 2^-18 W + 2^-20 |c|, which exceeds the rounding
+// of c -/+ W'' (<= eps (|c| + W'')).
+__device__ __forceinline__ void query_bins(float c, float W, float lo, float inv_w, int& b0, int& b1) {
+    const float Wp = __fadd_rn(__fadd_rn(__fmul_rn(W, 1.000003814697265625f), __fmul_rn(kKappa, fabsf(c))), kTau);
+    b0 = slope_bin(__fsub_rn(c, Wp), lo, inv_w);
+    b1 = slope_bin(__fadd_rn(c, Wp), lo, inv_w);
+}
+
+}  // namespace jpsi

@@ -1,0 +1,830 @@
+// Kernels of the J/psi first-level selection (arXiv:1810.11966, Sec. 3.2) on
+// sm_103a.  Work unit: one event (all of its stations).
+//
+//   k_light_count   one warp per event.  Each station's hits are staged from
+//                   HBM (coalesced loads, registers) into a per-warp shared
+//                   tile sorted into slope bins; pairs (L0, L1) that may
+//                   belong to a passing triplet go to a pair queue through
+//                   ballot/popc compaction; the queue is drained against the
+//                   L2 hits of the pair's bin window and every surviving
+//                   triple gets the exact FP32 fit (P1).  CHAIN mode keeps the
+//                   trigger triplets' slopes in the tile and searches the
+//                   other stations' tiles for compatible triplets (P2).
+//   k_generic       one block per event for events the warp tile cannot hold
+//                   (layer > 256 hits, station > 512 hits, > 64 trigger
+//                   triplets, or hits whose pruning bound is not finite).
+//                   Reads hits straight from global memory; pair pruning
+//                   only where it is proven (finite bounds).
+//   k_accept        accept bits from track counts (ballot per 32 events).
+//   k_scan*         exclusive scan of per-unit counts into int64 trip_off.
+//   *_emit          second pass when triplet lists are requested: the same
+//                   enumeration writes rows at trip_off[unit].
+//
+// Results never depend on the path an event takes: pruning only skips triples
+// that provably fail P1 (see jpsi_device.cuh), and P1/P2 are the same
+// correctly rounded FP32 expressions everywhere.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "jpsi_device.cuh"
+#include "jpsi_internal.h"
+
+namespace jpsi {
+
+constexpr int kRMax = 8;                  // hits per lane per layer (warp path)
+constexpr int kLayerCap = 32 * kRMax;     // 256 hits per layer
+constexpr int kHCap = 512;                // hits per station tile
+constexpr int kQCap = 256;                // pair queue entries
+constexpr int kTCap = 64;                 // trigger triplets per event (CHAIN)
+constexpr unsigned kFull = 0xffffffffu;
+
+struct LayerMeta {
+    float lo, inv_w, bmax;
+    int32_t base;   // global index of the layer's first hit
+    int32_t pbase;  // tile position of the layer's first stored hit
+    int32_t nlive;  // stored hits (finite coordinates)
+};
+
+struct WarpTile {
+    float4 P[kHCap];           // s_x, s_y, b, layer-local hit index (int bits), sorted by slope bin
+    uint32_t queue[kQCap];     // tile positions (p_i | p_j << 16)
+    float2 T[kTCap];           // trigger triplet slopes
+    uint8_t alive[kTCap];
+    uint16_t bst[3][kNB + 1];  // bin starts (tile positions) per layer
+    LayerMeta meta[3];
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, d));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
+    return v;
+}
+
+// ------------------------------------------------------- event offsets
+
+// The (3S+1) offsets of one event live in two registers per lane.
+struct EvOff {
+    int32_t a, b;
+};
+
+__device__ __forceinline__ int32_t off_get(const EvOff& o, int idx) {  // idx warp-uniform
+    return idx < 32 ? __shfl_sync(kFull, o.a, idx) : __shfl_sync(kFull, o.b, idx - 32);
+}
+
+// Loads and checks the event's CSR span: non-decreasing, first >= 0 (== 0
+// for event 0), last <= n_hits (== n_hits for the last event).
+__device__ bool warp_load_offsets(const Job& j, int64_t e, int lane, EvOff& o) {
+    const int S3 = j.S * 3;
+    const int32_t* base = j.off + e * S3;
+    o.a = lane <= S3 ? __ldg(base + lane) : 0;
+    o.b = 32 + lane <= S3 ? __ldg(base + 32 + lane) : 0;
+    int32_t na = __shfl_down_sync(kFull, o.a, 1);
+    const int32_t b0 = __shfl_sync(kFull, o.b, 0);
+    if (lane == 31) na = b0;
+    const int32_t nb = __shfl_down_sync(kFull, o.b, 1);
+    bool bad = (lane < S3 && na < o.a) || (32 + lane < S3 && nb < o.b);
+    const int32_t first = off_get(o, 0), last = off_get(o, S3);
+    if (lane == 0) {
+        if (first < 0 || (e == 0 && first != 0)) bad = true;
+        if ((int64_t)last > j.n_hits || (e == j.n_events - 1 && (int64_t)last != j.n_hits)) bad = true;
+    }
+    return !__any_sync(kFull, bad);
+}
+
+__device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? trig : (si - 1 < trig ? si - 1 : si); }
+
+// ------------------------------------------------------------- staging
+
+// Stages one layer into the tile.  Returns 0, or 1 (z <= 0), or 2 (a hit
+// whose pruning bound is not finite).
+__device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32_t n, int32_t pbase, int lane,
+                           int& nlive) {
+    float sx[kRMax], sy[kRMax], bb[kRMax];
+    bool lv[kRMax];
+    float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
+    bool zbad = false, wild = false;
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        lv[r] = false;
+        sx[r] = sy[r] = bb[r] = 0.0f;
+        const int h = lane + 32 * r;
+        if (32 * r < n && h < n) {
+            const HitPrep p = hit_prep(__ldg(j.x + base + h), __ldg(j.y + base + h), __ldg(j.z + base + h), j.K);
+            zbad |= p.zbad;
+            wild |= p.wild;
+            lv[r] = p.live && !p.wild;
+            sx[r] = p.sx;
+            sy[r] = p.sy;
+            bb[r] = p.b;
+            if (lv[r]) {
+                lo = fminf(lo, p.sx);
+                hi = fmaxf(hi, p.sx);
+                bmax = fmaxf(bmax, p.b);
+            }
+        }
+    }
+    if (__any_sync(kFull, zbad)) return 1;
+    if (__any_sync(kFull, wild)) return 2;
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    bmax = warp_max(bmax);
+    float inv_w = 0.0f;
+    if (hi > lo) {
+        inv_w = __fdiv_rn((float)kNB, __fsub_rn(hi, lo));
+        if (!isfinite(inv_w)) inv_w = 0.0f;
+    }
+    t.bst[l][lane] = 0;
+    __syncwarp();
+    int bin[kRMax], rank[kRMax];
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        bin[r] = 0;
+        rank[r] = 0;
+        if (32 * r < n) {
+            const int bn = lv[r] ? slope_bin(sx[r], lo, inv_w) : -1;
+            const unsigned peers = __match_any_sync(kFull, bn);
+            const int before = __popc(peers & lanemask_lt());
+            const int cur = lv[r] ? (int)t.bst[l][bn] : 0;
+            __syncwarp();
+            if (lv[r] && before == 0) t.bst[l][bn] = (uint16_t)(cur + __popc(peers));
+            __syncwarp();
+            bin[r] = bn;
+            rank[r] = cur + before;
+        }
+    }
+    const int cnt = t.bst[l][lane];
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    t.bst[l][lane] = (uint16_t)(pbase + incl - cnt);
+    if (lane == 31) t.bst[l][kNB] = (uint16_t)(pbase + total);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r)
+        if (lv[r]) t.P[t.bst[l][bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(lane + 32 * r));
+    if (lane == 0) {
+        LayerMeta m;
+        m.lo = lo;
+        m.inv_w = inv_w;
+        m.bmax = bmax;
+        m.base = base;
+        m.pbase = pbase;
+        m.nlive = total;
+        t.meta[l] = m;
+    }
+    __syncwarp();
+    nlive = total;
+    return 0;
+}
+
+__device__ int stage_station(const Job& j, WarpTile& t, int lane, const EvOff& o, int s) {
+    int pbase = 0;
+    for (int l = 0; l < 3; ++l) {
+        const int32_t b = off_get(o, s * 3 + l), e = off_get(o, s * 3 + l + 1);
+        int nl = 0;
+        const int st = stage_layer(j, t, l, b, e - b, pbase, lane, nl);
+        if (st) return st;
+        pbase += nl;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void layer_range(const WarpTile& t, int l, float c, float W, int& a, int& e) {
+    int b0, b1;
+    query_bins(c, W, t.meta[l].lo, t.meta[l].inv_w, b0, b1);
+    a = t.bst[l][b0];
+    e = t.bst[l][b1 + 1];
+}
+
+// ---------------------------------------------------------- enumeration
+
+// Drains the pair queue: every (i, j) against the L2 hits of both bin windows.
+template <bool EMIT>
+__device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn, bool collectT, int& nT,
+                      int32_t* rows, int limit, int& count) {
+    const float bmax2 = t.meta[2].bmax;
+    const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
+    for (int q0 = 0; q0 < qn; q0 += 32) {
+        const int q = q0 + lane;
+        const bool has = q < qn;
+        float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Pj = Pi;
+        int kb = 0, ke = 0, ii = 0, jj = 0;
+        float xi = 0.f, yi = 0.f, zi = 0.f, xj = 0.f, yj = 0.f, zj = 0.f;
+        if (has) {
+            const uint32_t en = t.queue[q];
+            Pi = t.P[en & 0xffffu];
+            Pj = t.P[en >> 16];
+            ii = __float_as_int(Pi.w);
+            jj = __float_as_int(Pj.w);
+            int a1, e1, a2, e2;
+            layer_range(t, 2, Pi.x, __fadd_rn(Pi.z, bmax2), a1, e1);
+            layer_range(t, 2, Pj.x, __fadd_rn(Pj.z, bmax2), a2, e2);
+            kb = max(a1, a2);
+            ke = min(e1, e2);
+            xi = __ldg(j.x + base0 + ii);
+            yi = __ldg(j.y + base0 + ii);
+            zi = __ldg(j.z + base0 + ii);
+            xj = __ldg(j.x + base1 + jj);
+            yj = __ldg(j.y + base1 + jj);
+            zj = __ldg(j.z + base1 + jj);
+        }
+        const int len = max(ke - kb, 0);
+        const int maxlen = __reduce_max_sync(kFull, len);
+        for (int tt = 0; tt < maxlen; ++tt) {
+            bool ok = false;
+            float mx = 0.f, my = 0.f;
+            int kk = 0;
+            if (tt < len) {
+                const float4 Pk = t.P[kb + tt];
+                if (pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) && pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
+                    kk = __float_as_int(Pk.w);
+                    const float xs[3] = {xi, xj, __ldg(j.x + base2 + kk)};
+                    const float ys[3] = {yi, yj, __ldg(j.y + base2 + kk)};
+                    const float zs[3] = {zi, zj, __ldg(j.z + base2 + kk)};
+                    ok = fit_pass(xs, ys, zs, c, mx, my);
+                }
+            }
+            const unsigned mask = __ballot_sync(kFull, ok);
+            if (mask) {
+                const int rank = __popc(mask & lanemask_lt());
+                if (EMIT && ok && count + rank < limit) {  // never past the unit's rows
+                    int32_t* r = rows + 3 * (int64_t)(count + rank);
+                    r[0] = ii;
+                    r[1] = jj;
+                    r[2] = kk;
+                }
+                if (collectT) {
+                    if (ok && nT + rank < kTCap) t.T[nT + rank] = make_float2(mx, my);
+                    nT += __popc(mask);
+                }
+                count += __popc(mask);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// All passing triplets of the staged station (Sec. 3.2 steps 1-2).
+template <bool EMIT>
+__device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts& c, bool collectT, int& nT,
+                                 int32_t* rows, int limit) {
+    const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
+    if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
+    const int p0 = t.meta[0].pbase;
+    const float bmax1 = t.meta[1].bmax;
+    int qn = 0, count = 0;
+    for (int i0 = 0; i0 < n0; i0 += 32) {
+        const int pi = p0 + i0 + lane;
+        const bool has = i0 + lane < n0;
+        float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int jb = 0, je = 0;
+        if (has) {
+            Pi = t.P[pi];
+            layer_range(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
+        }
+        const int len = je - jb;
+        const int maxlen = __reduce_max_sync(kFull, len);
+        for (int tt = 0; tt < maxlen; ++tt) {
+            bool pass = false;
+            const int pj = jb + tt;
+            if (tt < len) {
+                const float4 Pj = t.P[pj];
+                pass = pair_ok(Pi.x, Pi.y, Pi.z, Pj.x, Pj.y, Pj.z);
+            }
+            const unsigned mask = __ballot_sync(kFull, pass);
+            if (mask) {
+                if (pass) t.queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)pi | ((uint32_t)pj << 16);
+                qn += __popc(mask);
+                if (qn > kQCap - 32) {
+                    __syncwarp();
+                    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, count);
+                    qn = 0;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, count);
+    return count;
+}
+
+// Does station (staged in the tile) hold a passing triplet compatible with
+// the trigger slopes (mx, my)?  Per-lane search through the slope bins.
+__device__ bool road(const Job& j, const WarpTile& t, const Cuts& c, float mx, float my) {
+    int a[3], e[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+        layer_range(t, l, mx, __fadd_rn(t.meta[l].bmax, __fmul_rn(2.0f * kKappa, fabsf(mx))), a[l], e[l]);
+    const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
+    for (int p0 = a[0]; p0 < e[0]; ++p0) {
+        const float4 P0 = t.P[p0];
+        if (!tube_ok(P0.x, P0.y, P0.z, mx, my)) continue;
+        const int h0 = base0 + __float_as_int(P0.w);
+        const float x0 = __ldg(j.x + h0), y0 = __ldg(j.y + h0), z0 = __ldg(j.z + h0);
+        if (!tube_pass(x0, y0, z0, mx, my, c)) continue;
+        for (int p1 = a[1]; p1 < e[1]; ++p1) {
+            const float4 P1 = t.P[p1];
+            if (!tube_ok(P1.x, P1.y, P1.z, mx, my)) continue;
+            const int h1 = base1 + __float_as_int(P1.w);
+            const float x1 = __ldg(j.x + h1), y1 = __ldg(j.y + h1), z1 = __ldg(j.z + h1);
+            if (!tube_pass(x1, y1, z1, mx, my, c)) continue;
+            for (int p2 = a[2]; p2 < e[2]; ++p2) {
+                const float4 P2 = t.P[p2];
+                if (!tube_ok(P2.x, P2.y, P2.z, mx, my)) continue;
+                const int h2 = base2 + __float_as_int(P2.w);
+                const float xs[3] = {x0, x1, __ldg(j.x + h2)};
+                const float ys[3] = {y0, y1, __ldg(j.y + h2)};
+                const float zs[3] = {z0, z1, __ldg(j.z + h2)};
+                float fx, fy;
+                if (fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c)) return true;
+            }
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void to_generic(const Job& j, int64_t e, int lane) {
+    if (lane == 0) {
+        j.ev_class[e] = 1;
+        const int gi = atomicAdd(&j.ctrl->n_generic, 1);
+        j.glist[gi] = (int32_t)e;
+    }
+}
+
+__device__ void light_event_count(const Job& j, WarpTile& t, int lane, const Cuts& c, int64_t e) {
+    EvOff o;
+    const int S = j.S;
+    if (!warp_load_offsets(j, e, lane, o)) {
+        if (lane == 0) {
+            atomicOr(&j.ctrl->status, kStInvalid);
+            j.ev_class[e] = 2;
+        }
+        return;
+    }
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    bool fits = true;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        const int32_t o0 = off_get(o, 3 * s), o1 = off_get(o, 3 * s + 1), o2 = off_get(o, 3 * s + 2),
+                      o3 = off_get(o, 3 * s + 3);
+        if (o1 - o0 > kLayerCap || o2 - o1 > kLayerCap || o3 - o2 > kLayerCap || o3 - o0 > kHCap) fits = false;
+    }
+    if (!fits) {
+        to_generic(j, e, lane);
+        return;
+    }
+    int nT = 0, trig_count = 0;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        const int st = stage_station(j, t, lane, o, s);
+        if (st == 1) {
+            if (lane == 0) {
+                atomicOr(&j.ctrl->status, kStInvalid);
+                j.ev_class[e] = 2;
+            }
+            return;
+        }
+        if (st == 2) {
+            to_generic(j, e, lane);
+            return;
+        }
+        const bool collect = chain && s == j.trig;
+        const int cnt = enumerate_station<false>(j, t, lane, c, collect, nT, nullptr, 0);
+        if (collect) {
+            if (nT > kTCap) {
+                to_generic(j, e, lane);
+                return;
+            }
+            for (int i = lane; i < nT; i += 32) t.alive[i] = 1;
+            __syncwarp();
+        }
+        if (s == j.trig) trig_count = cnt;
+        if (lane == 0) j.unit_counts[e * S + s] = cnt;
+        if (chain && s != j.trig && nT > 0) {
+            for (int ti = lane; ti < nT; ti += 32)
+                if (t.alive[ti]) {
+                    const float2 m = t.T[ti];
+                    if (!road(j, t, c, m.x, m.y)) t.alive[ti] = 0;
+                }
+            __syncwarp();
+        }
+    }
+    if (j.mode == 0 && lane < S && lane != j.trig) j.unit_counts[e * S + lane] = 0;
+    int tc = trig_count;
+    if (chain) {
+        int a = 0;
+        for (int ti = lane; ti < nT; ti += 32) a += t.alive[ti];
+        tc = __reduce_add_sync(kFull, a);
+    }
+    if (lane == 0) {
+        j.track_counts[e] = tc;
+        j.ev_class[e] = 0;
+    }
+}
+
+__device__ void light_event_emit(const Job& j, WarpTile& t, int lane, const Cuts& c, int64_t e) {
+    if (j.ev_class[e] != 0) return;
+    const int S = j.S;
+    const int nproc = j.mode == 1 ? S : 1;
+    bool any = false;
+    for (int si = 0; si < nproc; ++si) any |= j.unit_counts[e * S + station_of(si, j.trig)] != 0;
+    if (!any) return;
+    EvOff o;
+    warp_load_offsets(j, e, lane, o);
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        const int64_t u = e * S + s;
+        const int cnt = j.unit_counts[u];
+        if (cnt == 0) continue;
+        if (stage_station(j, t, lane, o, s) != 0) {
+            if (lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
+            return;
+        }
+        int nT = 0;
+        const int got = enumerate_station<true>(j, t, lane, c, false, nT, j.triplets + 3 * j.trip_off[u], cnt);
+        if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
+    }
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_light(const Job* __restrict__ djob, int persistent) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Job j = *djob;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpTile& t = reinterpret_cast<WarpTile*>(smem_raw)[w];
+    const Cuts c{j.cx, j.cy, j.K};
+    if (persistent) {
+        unsigned long long* ctr = &j.ctrl->work[EMIT ? 2 : 0];
+        for (;;) {
+            long long e0 = 0;
+            if (lane == 0) e0 = (long long)atomicAdd(ctr, (unsigned long long)j.grab);
+            e0 = __shfl_sync(kFull, e0, 0);
+            if (e0 >= j.n_events) break;
+            const long long e1 = min(e0 + (long long)j.grab, (long long)j.n_events);
+            for (long long e = e0; e < e1; ++e) {
+                if (EMIT)
+                    light_event_emit(j, t, lane, c, e);
+                else
+                    light_event_count(j, t, lane, c, e);
+            }
+        }
+    } else {
+        const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+        if (e < j.n_events) {
+            if (EMIT)
+                light_event_emit(j, t, lane, c, e);
+            else
+                light_event_count(j, t, lane, c, e);
+        }
+    }
+}
+
+// ----------------------------------------------- block-per-event kernel
+
+struct GHit {
+    float x, y, z;
+    HitPrep p;
+};
+
+__device__ __forceinline__ GHit ghit(const Job& j, int64_t h) {
+    GHit g;
+    g.x = __ldg(j.x + h);
+    g.y = __ldg(j.y + h);
+    g.z = __ldg(j.z + h);
+    g.p = hit_prep(g.x, g.y, g.z, j.K);
+    return g;
+}
+
+// Brute-force P2 search over every hit of every other station.
+__device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, float mx, float my) {
+    for (int s = 0; s < j.S; ++s) {
+        if (s == j.trig) continue;
+        const int32_t* o = soff + 3 * s;
+        bool found = false;
+        for (int32_t h0 = o[0]; h0 < o[1] && !found; ++h0) {
+            const float x0 = __ldg(j.x + h0), y0 = __ldg(j.y + h0), z0 = __ldg(j.z + h0);
+            if (!tube_pass(x0, y0, z0, mx, my, c)) continue;
+            for (int32_t h1 = o[1]; h1 < o[2] && !found; ++h1) {
+                const float x1 = __ldg(j.x + h1), y1 = __ldg(j.y + h1), z1 = __ldg(j.z + h1);
+                if (!tube_pass(x1, y1, z1, mx, my, c)) continue;
+                for (int32_t h2 = o[2]; h2 < o[3] && !found; ++h2) {
+                    const float xs[3] = {x0, x1, __ldg(j.x + h2)};
+                    const float ys[3] = {y0, y1, __ldg(j.y + h2)};
+                    const float zs[3] = {z0, z1, __ldg(j.z + h2)};
+                    if (!tube_pass(xs[2], ys[2], zs[2], mx, my, c)) continue;
+                    float fx, fy;
+                    found = fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c);
+                }
+            }
+        }
+        if (!found) return false;
+    }
+    return true;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
+    __shared__ int32_t soff[3 * kMaxStations + 1];
+    __shared__ int s_gi, s_count, s_cand, s_bad;
+    const Job j = *djob;
+    const Cuts c{j.cx, j.cy, j.K};
+    const int n_gen = *(volatile int32_t*)&j.ctrl->n_generic;
+    const int S = j.S, S3 = 3 * S;
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 3 : 1], 1ull);
+        __syncthreads();
+        const int gi = s_gi;
+        if (gi >= n_gen) break;
+        const int64_t e = j.glist[gi];
+        for (int i = threadIdx.x; i <= S3; i += blockDim.x) soff[i] = j.off[e * S3 + i];
+        if (threadIdx.x == 0) s_cand = 0;
+        __syncthreads();
+        int trig_count = 0;
+        bool bad_event = false;
+        for (int si = 0; si < nproc && !bad_event; ++si) {
+            const int s = station_of(si, j.trig);
+            const int64_t u = e * S + s;
+            const int32_t* o = soff + 3 * s;
+            if (EMIT && j.unit_counts[u] == 0) continue;
+            if (threadIdx.x == 0) {
+                s_count = 0;
+                s_bad = 0;
+            }
+            __syncthreads();
+            if (!EMIT) {
+                for (int32_t h = o[0] + threadIdx.x; h < o[3]; h += blockDim.x)
+                    if (__ldg(j.z + h) <= 0.0f) s_bad = 1;
+                __syncthreads();
+                if (s_bad) {
+                    if (threadIdx.x == 0) atomicOr(&j.ctrl->status, kStInvalid);
+                    bad_event = true;
+                    break;
+                }
+            }
+            const int64_t n0 = o[1] - o[0], n1 = o[2] - o[1], n2 = o[3] - o[2];
+            const int64_t npairs = n0 * n1;
+            int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
+            const int ulimit = EMIT ? j.unit_counts[u] : 0;
+            int local = 0;
+            const bool collect = !EMIT && chain && s == j.trig;
+            for (int64_t p = threadIdx.x; p < npairs; p += blockDim.x) {
+                const int64_t i = p / n1, jx = p - i * n1;
+                const GHit hi = ghit(j, o[0] + i), hj = ghit(j, o[1] + jx);
+                if (!hi.p.live || !hj.p.live) continue;
+                if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hi.p.b, hj.p.sx, hj.p.sy, hj.p.b)) continue;
+                for (int64_t k = 0; k < n2; ++k) {
+                    const GHit hk = ghit(j, o[2] + k);
+                    if (!hk.p.live) continue;
+                    if (!hk.p.wild) {
+                        if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hi.p.b, hk.p.sx, hk.p.sy, hk.p.b)) continue;
+                        if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hj.p.b, hk.p.sx, hk.p.sy, hk.p.b)) continue;
+                    }
+                    const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
+                    float mx, my;
+                    if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
+                    ++local;
+                    if (EMIT) {
+                        const int pos = atomicAdd(&s_count, 1);
+                        if (pos < ulimit) {  // never past the unit's rows
+                            int32_t* r = rows + 3 * (int64_t)pos;
+                            r[0] = (int32_t)i;
+                            r[1] = (int32_t)jx;
+                            r[2] = (int32_t)k;
+                        }
+                    }
+                    if (collect && road_global(j, soff, c, mx, my)) atomicAdd(&s_cand, 1);
+                }
+            }
+            if (!EMIT && local) atomicAdd(&s_count, local);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (EMIT) {
+                    if (s_count != j.unit_counts[u]) atomicOr(&j.ctrl->status, kStEmitMismatch);
+                } else {
+                    j.unit_counts[u] = s_count;
+                }
+            }
+            if (s == j.trig) trig_count = s_count;
+            __syncthreads();
+        }
+        if (!EMIT && !bad_event && threadIdx.x == 0) {
+            if (j.mode == 0)
+                for (int s = 0; s < S; ++s)
+                    if (s != j.trig) j.unit_counts[e * S + s] = 0;
+            j.track_counts[e] = chain ? s_cand : trig_count;
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------- accept bits
+
+__global__ void k_accept(const Job* __restrict__ djob) {
+    const Job j = *djob;
+    if (!j.accept_bits) return;
+    const int64_t nwords = (j.n_events + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwords; w += wstride) {
+        const int64_t e = w * 32 + lane;
+        const bool v = e < j.n_events && j.track_counts[e] >= j.minc;
+        const unsigned bits = __ballot_sync(kFull, v);
+        if (lane == 0) j.accept_bits[w] = bits;
+    }
+}
+
+// --------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t& total) {
+    // sh: kScanThreads/32 + 1 entries
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int64_t s = lane < nw ? sh[lane] : 0;
+        int64_t si = s;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(kFull, si, d);
+            if (lane >= d) si += o;
+        }
+        if (lane < nw) sh[lane] = si - s;
+        if (lane == 31) sh[32] = si;
+    }
+    __syncthreads();
+    const int64_t r = sh[w] + incl - v;
+    total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Job* __restrict__ djob) {
+    __shared__ int64_t sh[33];
+    const Job j = *djob;
+    const int64_t n = j.n_events * j.S;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int64_t v = 0;
+        const int64_t b = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q)
+            if (b + q < n) v += j.unit_counts[b + q];
+        int64_t total;
+        block_excl_scan(v, sh, total);
+        if (threadIdx.x == 0) j.block_sums[tile] = total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(const Job* __restrict__ djob) {
+    __shared__ int64_t sh[33];
+    const Job j = *djob;
+    const int64_t n = j.n_events * j.S;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    int64_t carry = 0;
+    for (int64_t b = 0; b < ntiles; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t v = i < ntiles ? j.block_sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_excl_scan(v, sh, total);
+        if (i < ntiles) j.block_sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        j.trip_off[n] = carry;
+        j.ctrl->trip_total = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const Job* __restrict__ djob) {
+    __shared__ int64_t sh[33];
+    const Job j = *djob;
+    const int64_t n = j.n_events * j.S;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t b = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+        int32_t v[kScanItems];
+        int64_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            v[q] = b + q < n ? j.unit_counts[b + q] : 0;
+            sum += v[q];
+        }
+        int64_t total;
+        int64_t run = block_excl_scan(sum, sh, total) + j.block_sums[tile];
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q)
+            if (b + q < n) {
+                j.trip_off[b + q] = run;
+                run += v[q];
+            }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile); }
+
+static bool g_attr_done = false;
+
+static cudaError_t ensure_attrs() {
+    if (g_attr_done) return cudaSuccess;
+    const int maxw = 8;
+    cudaError_t e = cudaFuncSetAttribute(k_light<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)light_smem_bytes(maxw));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_light<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)light_smem_bytes(maxw));
+    if (e == cudaSuccess) g_attr_done = true;
+    return e;
+}
+
+int light_max_blocks_per_sm(int wpb) {
+    if (ensure_attrs() != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_light<false>, wpb * 32, light_smem_bytes(wpb)) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int generic_max_blocks_per_sm(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_generic<false>, threads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+const void* light_count_kernel_ptr() { return (const void*)k_light<false>; }
+
+cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+                               cudaStream_t st) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    const int wpb = lc.light_wpb;
+    const size_t smem = light_smem_bytes(wpb);
+    if (persistent) {
+        k_light<false><<<lc.light_blocks, wpb * 32, smem, st>>>(djob, 1);
+    } else {
+        const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
+        k_light<false><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
+    k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
+    k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(djob);
+    k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+                              cudaStream_t st) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    const int wpb = lc.light_wpb;
+    const size_t smem = light_smem_bytes(wpb);
+    if (persistent) {
+        k_light<true><<<lc.light_blocks, wpb * 32, smem, st>>>(djob, 1);
+    } else {
+        const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
+        k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
+    }
+    k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
+    return cudaGetLastError();
+}
+
+}  // namespace jpsi

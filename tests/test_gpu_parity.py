@@ -1,0 +1,225 @@
+"""GPU library (through the C ABI) == oracle, bit-exact, on seeded inputs of
+every workload shape, plus the edge cases and error paths of the contract."""
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_same, gpu_select
+from helpers import line_event, make_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1810_11966_gb300 as jp
+    jp.load(build_if_missing=True)
+    return jp
+
+
+def _ctx(lib, S=4, mode=1, t_xz=0.25, t_yz=None, **kw):
+    return lib.Context(lib.params(S, mode, t_xz=t_xz, t_yz=t_yz), **kw)
+
+
+def _oracle(oracle_mod, S, mode, t_xz, t_yz, batch, threads=8):
+    return oracle_mod.run(oracle_mod.params(S, mode, t_xz=t_xz, t_yz=t_yz), batch, n_threads=threads)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("cuts", [(0.25, 0.25), (0.03, 0.025)])
+@pytest.mark.parametrize("form", ["plain", "batched"])
+def test_small_workload(lib, oracle_mod, synth_mod, mode, cuts, form):
+    b = synth_mod.generate("poisson20_1k")
+    ref = _oracle(oracle_mod, 4, mode, *cuts, b)
+    ctx = _ctx(lib, 4, mode, *cuts)
+    g = gpu_select(ctx, b, form=form)
+    assert_same(g, ref, 4000, label=f"mode{mode} {cuts} {form}")
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_poisson100_slice(lib, oracle_mod, synth_mod, mode):
+    # 3 000 events of the 10^6-event workload: several warp tiles, full bins
+    b = synth_mod.generate("poisson100_1m", 0, 3000)
+    ref = _oracle(oracle_mod, 4, mode, 0.25, 0.25, b)
+    ctx = _ctx(lib, 4, mode)
+    for form in ("plain", "batched"):
+        assert_same(gpu_select(ctx, b, form=form), ref, 12000, label=form)
+
+
+def test_lognormal_timeslice(lib, oracle_mod, synth_mod):
+    # log-normal multiplicities: light events on warps, heavy ones on blocks
+    b = synth_mod.generate("lognormal_timeslices", 0, 2500)
+    counts = np.diff(b["offsets"]).reshape(-1, 12)
+    assert counts.max() > 256  # exercises the block-per-event path
+    ref = _oracle(oracle_mod, 4, 1, 0.25, 0.25, b)
+    ctx = _ctx(lib, 4, 1)
+    for form in ("plain", "batched"):
+        assert_same(gpu_select(ctx, b, form=form), ref, 10000, label=form)
+
+
+def test_stress_subset(lib, oracle_mod, synth_mod):
+    # 6 stations x 1500 hits per layer, window 1.0 cm: ~10^4 triplets per unit
+    b = synth_mod.generate("poisson1500_6st", 0, 60)
+    ref = _oracle(oracle_mod, 6, 1, 1.0, 1.0, b, threads=16)
+    assert ref["trip_needed"] > 60 * 6 * 1000
+    ctx = _ctx(lib, 6, 1, 1.0)
+    assert_same(gpu_select(ctx, b), ref, 360)
+
+
+def test_adversarial_events(lib, oracle_mod):
+    rng = np.random.default_rng(21)
+    events = []
+    # near-threshold straight tracks + background
+    for _ in range(60):
+        tracks = [tuple(rng.uniform(-0.35, 0.35, 2)) for _ in range(3)]
+        events.append(line_event(2, tracks, rng=rng, sigma=0.3, extra_bg=8))
+    # odd magnitudes, NaN, Inf, subnormal and huge z (z > 0 everywhere)
+    odd = np.array([0.0, 1e-38, 1e-42, 3e38, -3e38, 1e20, -1e-20, np.nan, np.inf, -np.inf, 5.0, -5.0],
+                   np.float32)
+    zodd = np.array([1e-42, 1e-20, 1.0, 130.0, 3e38, np.inf, np.nan], np.float32)
+    for _ in range(40):
+        ev = []
+        for _l in range(6):
+            ev.append([(rng.choice(odd), rng.choice(odd), rng.choice(zodd)) for _ in range(rng.integers(0, 5))])
+        events.append(ev)
+    # empty event, one-hit event, empty middle layer
+    events.append([[] for _ in range(6)])
+    events.append([[(1.0, 1.0, 120.0)]] + [[] for _ in range(5)])
+    zl = [120.0, 130.0, 140.0, 155.0, 165.0, 175.0]
+    events.append([[(0.1 * z, 0.1 * z, z)] if li != 4 else [] for li, z in enumerate(zl)])
+    b = make_batch(events, 2)
+    for t in (0.0, 0.25, 1e30):
+        for mode in (0, 1):
+            ref = _oracle(oracle_mod, 2, mode, t, t, b)
+            assert ref["status"] == 0
+            ctx = _ctx(lib, 2, mode, t, t)
+            for form in ("plain", "batched"):
+                assert_same(gpu_select(ctx, b, form=form), ref, len(events) * 2, label=f"t={t} mode={mode} {form}")
+
+
+def test_one_station_and_trigger_choice(lib, oracle_mod, synth_mod):
+    b = synth_mod.generate("poisson20_1k", 0, 400)
+    b1 = dict(b, n_events=b["n_events"] * 4, n_stations=1)
+    for mode in (0, 1):
+        ref = _oracle(oracle_mod, 1, mode, 0.25, 0.25, b1)
+        assert_same(gpu_select(_ctx(lib, 1, mode), b1), ref, 1600)
+    # trigger station in the middle
+    ref = oracle_mod.run(oracle_mod.params(4, 1, t_xz=0.25, trigger_station=1), b, n_threads=8)
+    ctx = lib.Context(lib.params(4, 1, t_xz=0.25, trigger_station=1))
+    assert_same(gpu_select(ctx, b), ref, 1600)
+
+
+def test_zero_events(lib):
+    ctx = _ctx(lib)
+    b = make_batch([], 4)
+    g = gpu_select(ctx, b)
+    assert g["status"] == 0 and g["trip_needed"] == 0 and g["trip_off"][0] == 0
+
+
+def test_many_tiny_events_ragged(lib, oracle_mod):
+    # 70 001 events (not a multiple of any block), most with empty layers
+    rng = np.random.default_rng(8)
+    n = 70001
+    counts = rng.integers(0, 3, size=(n, 6)).astype(np.int32)
+    counts[rng.random(n) < 0.5] = 0
+    off = np.zeros(counts.size + 1, np.int64)
+    np.cumsum(counts.reshape(-1), out=off[1:])
+    nh = int(off[-1])
+    z = np.repeat(np.tile(np.array([120, 130, 140, 155, 165, 175], np.float32), n), counts.reshape(-1))
+    t = rng.uniform(-0.1, 0.1, nh).astype(np.float32)
+    b = {"x": (t * z + rng.normal(0, 0.2, nh)).astype(np.float32),
+         "y": (t * z + rng.normal(0, 0.2, nh)).astype(np.float32),
+         "z": z, "offsets": off.astype(np.int32), "n_events": n, "n_hits": nh}
+    ref = _oracle(oracle_mod, 2, 1, 0.25, 0.25, b)
+    assert_same(gpu_select(_ctx(lib, 2, 1), b), ref, 2 * n)
+
+
+def test_invalid_inputs(lib, synth_mod):
+    b = synth_mod.generate("poisson20_1k", 0, 50)
+    ctx = _ctx(lib)
+    bad = dict(b, offsets=b["offsets"].copy())
+    bad["offsets"][30] = bad["offsets"][31] + 5
+    assert gpu_select(ctx, bad, triplets=False)["status"] == lib.JPSI_EINVAL
+    bad = dict(b, offsets=b["offsets"].copy())
+    bad["offsets"][-1] -= 1
+    assert gpu_select(ctx, dict(bad, n_hits=b["n_hits"]), triplets=False)["status"] == lib.JPSI_EINVAL
+    zb = b["z"].copy()
+    zb[100] = -1.0
+    assert gpu_select(ctx, dict(b, z=zb), triplets=False)["status"] == lib.JPSI_EINVAL
+    # the context stays usable after an error
+    assert gpu_select(ctx, b)["status"] == 0
+
+
+def test_host_pointer_rejected(lib, synth_mod):
+    import ctypes
+    ctx = _ctx(lib)
+    b = synth_mod.generate("poisson20_1k", 0, 10)
+    hb = lib.make_batch(b["x"], b["y"], b["z"], b["offsets"], 10)
+    o = lib.jpsi_outputs()
+    import torch
+    tc = torch.empty(10, dtype=torch.int32, device="cuda")
+    o.track_counts = tc.data_ptr()
+    s = lib.jpsi_run(ctx.ctx, hb, o, torch.cuda.current_stream().cuda_stream)
+    # pageable host memory is only accepted where the device can address it
+    if s != lib.JPSI_OK:
+        assert s == lib.JPSI_EINVAL
+
+
+def test_capacity_and_retry(lib, oracle_mod, synth_mod):
+    b = synth_mod.generate("poisson20_1k", 0, 300)
+    ref = _oracle(oracle_mod, 4, 1, 0.25, 0.25, b)
+    ctx = _ctx(lib)
+    g = gpu_select(ctx, b, capacity=ref["trip_needed"] - 1)
+    assert g["status"] == lib.JPSI_ECAPACITY and g["trip_needed"] == ref["trip_needed"]
+    assert np.array_equal(g["track_counts"], ref["track_counts"])
+    assert np.array_equal(g["trip_off"], ref["trip_off"])
+    g = gpu_select(ctx, b, capacity=g["trip_needed"])
+    assert_same(g, ref, 1200)
+
+
+def test_budget_enomem(lib, synth_mod):
+    b = synth_mod.generate("poisson20_1k", 0, 1000)
+    ctx = _ctx(lib, hbm_budget=4096)
+    g = gpu_select(ctx, b, triplets=False)
+    assert g["status"] == lib.JPSI_ENOMEM
+
+
+def test_plain_equals_batched_and_deterministic(lib, synth_mod):
+    b = synth_mod.generate("poisson100_1m", 5000, 20000)
+    ctx = _ctx(lib)
+    a = gpu_select(ctx, b, form="plain")
+    for _ in range(2):
+        c = gpu_select(ctx, b, form="batched")
+        assert_same(c, a, 80000)
+
+
+def test_run_host_matches_device(lib, synth_mod):
+    import ctypes
+    b = synth_mod.generate("poisson20_1k", 0, 700)
+    ctx = _ctx(lib)
+    dev = gpu_select(ctx, b)
+    n = 700
+    acc = np.zeros((n + 31) // 32, np.uint32)
+    tc = np.zeros(n, np.int32)
+    to = np.zeros(n * 4 + 1, np.int64)
+    tr = np.zeros((dev["trip_needed"] + 5, 3), np.int32)
+    o = lib.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off, o.triplets = acc.ctypes.data, tc.ctypes.data, to.ctypes.data, tr.ctypes.data
+    o.trip_capacity = len(tr)
+    hb = lib.make_batch(b["x"], b["y"], b["z"], b["offsets"], n)
+    s = lib.jpsi_run_host(ctx.ctx, hb, o, 0)
+    assert s == 0 and o.trip_needed == dev["trip_needed"]
+    host = {"status": 0, "trip_needed": o.trip_needed, "accept_bits": acc, "track_counts": tc, "trip_off": to,
+            "triplets": tr[: o.trip_needed]}
+    assert_same(host, dev, n * 4)
+
+
+def test_autotune_keeps_results(lib, synth_mod):
+    import torch
+    b = synth_mod.generate("lognormal_timeslices", 0, 4000)
+    ctx = _ctx(lib)
+    before = gpu_select(ctx, b)
+    d = {k: torch.from_numpy(b[k]).cuda() for k in ("x", "y", "z", "offsets")}
+    s = lib.jpsi_autotune(ctx.ctx, lib.make_batch(d["x"], d["y"], d["z"], d["offsets"], 4000))
+    assert s == 0
+    after = gpu_select(ctx, b)
+    assert_same(after, before, 16000)
