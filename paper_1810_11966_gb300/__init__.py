@@ -235,11 +235,12 @@ class Context:
             raise JpsiError(s, self.last_error())
 
     def select(self, x, y, z, offsets, n_events, *, triplets=True, capacity=None, form="batched", stream=None):
-        """Runs the selection on device tensors.  Returns a dict of device
-        tensors: accept_bits, track_counts, trip_off, triplets ([n,3]) and
-        trip_needed.  With capacity=None the call sizes the triplet buffer
-        from a first counting run (two calls, like the library's own
-        two-pass contract)."""
+        """Runs the selection on device tensors.  Returns a dict with the run's
+        status and the device tensors accept_bits, track_counts, trip_off,
+        triplets ([n,3]) and trip_needed (statuses are returned, not
+        raised).  With capacity=None the call sizes the triplet buffer from a
+        first counting run (two calls, like the library's own two-pass
+        contract)."""
         import torch
         dev = torch.device("cuda", self.device)
         S = self.p.n_stations
@@ -256,23 +257,22 @@ class Context:
         o.trip_off = out["trip_off"].data_ptr()
         run = {"batched": jpsi_run, "plain": jpsi_run_plain}[form]
         st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        tr = None
         if triplets:
             if capacity is None:
                 s = run(self.ctx, b, o, st)
-                self.check(s)
+                if s != JPSI_OK:
+                    out.update(status=s, trip_needed=o.trip_needed, triplets=None, error=self.last_error())
+                    return out
                 capacity = o.trip_needed
             tr = torch.empty((max(capacity, 1), 3), dtype=torch.int32, device=dev)
             o.triplets = tr.data_ptr()
             o.trip_capacity = capacity
         s = run(self.ctx, b, o, st)
         out["status"] = s
+        out["error"] = self.last_error() if s != JPSI_OK else ""
         out["trip_needed"] = o.trip_needed
-        if s not in (JPSI_OK, JPSI_ECAPACITY):
-            self.check(s)
-        if triplets and s == JPSI_OK:
-            out["triplets"] = tr[: o.trip_needed]
-        else:
-            out["triplets"] = None
+        out["triplets"] = tr[: o.trip_needed] if (triplets and s == JPSI_OK) else None
         out["accept_bits"] = out["accept_bits"][: (n_events + 31) // 32]
         out["track_counts"] = out["track_counts"][:n_events]
         return out

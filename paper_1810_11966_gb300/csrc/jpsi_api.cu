@@ -43,8 +43,9 @@ struct RunState {
     Job* h_job = nullptr;     // pinned
     Ctrl* d_ctrl = nullptr;
     Ctrl* h_ctrl = nullptr;   // pinned
-    DevBuf unit_counts, track_counts, ev_class, glist, block_sums, trip_off;
-    cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr;
+    DevBuf unit_counts, track_counts, ev_class, glist, block_sums, trip_off, tscr;
+    int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
+    cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr, g_scatter = nullptr;
     int g_cfg_id = -1;
     cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
 };
@@ -239,6 +240,18 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.trip_off = o->trip_off ? o->trip_off : (int64_t*)rs.trip_off.p;
     j.block_sums = (int64_t*)rs.block_sums.p;
     j.triplets = o->triplets;
+    j.tscr = nullptr;
+    j.tscr_cap = 0;
+    if (o->triplets) {
+        // entries of the counting pass; without room for them the triplets are
+        // written by re-enumeration instead (same result, slower)
+        const size_t want = (size_t)std::min<int64_t>(rs.tscr_want, std::max<int64_t>(o->trip_capacity, 1)) * sizeof(TripEntry);
+        const bool fits = want <= rs.tscr.bytes || c->used + (want - rs.tscr.bytes) <= c->budget;
+        if (fits && ensure(c, rs.tscr, want, "triplet entries") == JPSI_OK) {
+            j.tscr = (TripEntry*)rs.tscr.p;
+            j.tscr_cap = (int64_t)(rs.tscr.bytes / sizeof(TripEntry));
+        }
+    }
     j.ctrl = rs.d_ctrl;
     return JPSI_OK;
 }
@@ -257,7 +270,7 @@ jpsi_status state_init(jpsi_ctx* c, RunState& rs) {
 }
 
 void destroy_graphs(RunState& rs) {
-    cudaGraphExec_t* gs[] = {&rs.g_light, &rs.g_rest, &rs.g_emit};
+    cudaGraphExec_t* gs[] = {&rs.g_light, &rs.g_rest, &rs.g_emit, &rs.g_scatter};
     for (cudaGraphExec_t* g : gs) {
         if (*g) cudaGraphExecDestroy(*g);
         *g = nullptr;
@@ -284,6 +297,7 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.glist);
     release(c, rs.block_sums);
     release(c, rs.trip_off);
+    release(c, rs.tscr);
 }
 
 // Captures the count and emit phases of the batched form into graphs that
@@ -292,13 +306,14 @@ jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
     if (rs.g_light && rs.g_cfg_id == c->cfg_id) return JPSI_OK;
     std::lock_guard<std::mutex> cap_lock(c->cap_mu);
     destroy_graphs(rs);
-    for (int phase = 0; phase < 3; ++phase) {
+    for (int phase = 0; phase < 4; ++phase) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
         cudaError_t le = phase == 0   ? launch_light_count(rs.d_job, 0, c->batch_cfg, true, c->cap_stream)
                          : phase == 1 ? launch_count_rest(rs.d_job, c->batch_cfg, c->cap_stream)
-                                      : launch_emit_phase(rs.d_job, 0, c->batch_cfg, true, c->cap_stream);
+                         : phase == 2 ? launch_emit_phase(rs.d_job, 0, c->batch_cfg, true, c->cap_stream)
+                                      : launch_scatter(rs.d_job, c->batch_cfg, c->cap_stream);
         e = cudaStreamEndCapture(c->cap_stream, &g);
         if (le != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -309,7 +324,7 @@ jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
         e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-        (phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : rs.g_emit) = ge;
+        (phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : phase == 2 ? rs.g_emit : rs.g_scatter) = ge;
     }
     rs.g_cfg_id = c->cfg_id;
     return JPSI_OK;
@@ -368,11 +383,20 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         add_timing(c, rs, launches, false);
         return JPSI_OK;
     }
+    // triplet rows: scatter the recorded entries, or re-enumerate when they
+    // did not fit (then record more next time, within the budget)
+    const bool scattered = rs.h_job->tscr && !(ctl.status & kStNoScratch) &&
+                           ctl.scratch_n <= (unsigned long long)rs.h_job->tscr_cap;
+    if (!scattered && rs.h_job->tscr && !(ctl.status & kStNoScratch))
+        rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
     if (timing) cudaEventRecord(rs.ev[3], st);
-    e = batched ? cudaGraphLaunch(rs.g_emit, st) : launch_emit_phase(rs.d_job, ne, c->plain_cfg, false, st);
+    if (scattered)
+        e = batched ? cudaGraphLaunch(rs.g_scatter, st) : launch_scatter(rs.d_job, c->plain_cfg, st);
+    else
+        e = batched ? cudaGraphLaunch(rs.g_emit, st) : launch_emit_phase(rs.d_job, ne, c->plain_cfg, false, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "emit");
     if (timing) cudaEventRecord(rs.ev[4], st);
-    launches += kLaunchesEmit;
+    launches += scattered ? kLaunchesScatter : kLaunchesEmit;
     if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "ctrl readback");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "emit phase");

@@ -27,7 +27,7 @@ namespace jpsi {
 
 constexpr float kKappa = 9.5367431640625e-07f;  // 2^-20
 constexpr float kTau = 1e-37f;
-constexpr int kNB = 32;                          // slope bins per layer
+constexpr int kNB = 64;                          // slope bins per layer
 
 struct Cuts {
     float cx, cy;  // thresholds on S_x, S_y: fl32(ndf * t)

@@ -13,7 +13,19 @@ constexpr int kMaxStations = 16;
 enum : int32_t {
     kStInvalid = 1,        // malformed offsets or z <= 0
     kStEmitMismatch = 2,   // emit pass found a different count than the count pass (internal error)
+    kStNoScratch = 4,      // a triplet index did not fit the scratch entry format
 };
+
+// A passing triplet recorded by the counting pass: unit, rank inside the
+// unit, and (i, j, k) packed 21 bits each; bit 63 marks entries written by
+// the block-per-event kernel.
+struct TripEntry {
+    int32_t unit;
+    int32_t rank;
+    unsigned long long ijk;
+};
+constexpr unsigned long long kFromGeneric = 1ull << 63;
+constexpr int32_t kPackLimit = 1 << 21;
 
 // Device-resident control block of one run (zeroed before each run).
 struct Ctrl {
@@ -21,7 +33,7 @@ struct Ctrl {
     int32_t n_generic;            // events sent to the block-per-event kernel
     unsigned long long work[4];   // persistent work counters: light count, generic count, light emit, generic emit
     int64_t trip_total;           // copy of trip_off[n_units]
-    int32_t pad[2];
+    unsigned long long scratch_n; // triplet entries appended by the counting pass
 };
 
 // Everything a run's kernels read; lives in device memory so a captured
@@ -44,6 +56,8 @@ struct Job {
     int64_t* trip_off;            // [n_units + 1]
     int64_t* block_sums;          // scan scratch
     int32_t* triplets;            // may be null
+    TripEntry* tscr;              // counting-pass triplet entries (null: not recorded)
+    int64_t tscr_cap;
     Ctrl* ctrl;
 };
 
@@ -62,7 +76,11 @@ cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCf
                                cudaStream_t st);
 cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesLight = 1, kLaunchesRest = 5, kLaunchesEmit = 2;
-// Emit phase: light emit kernel and block-per-event emit kernel.
+// Places the counting pass's triplet entries at trip_off[unit] + rank.
+cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+constexpr int kLaunchesScatter = 1;
+// Emit phase (fallback when the entries overflowed): light emit kernel and
+// block-per-event emit kernel re-enumerate the units.
 cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
                               cudaStream_t st);
 size_t light_smem_bytes(int wpb);

@@ -11,7 +11,7 @@
 //                   trigger triplets' slopes in the tile and searches the
 //                   other stations' tiles for compatible triplets (P2).
 //   k_generic       one block per event for events the warp tile cannot hold
-//                   (layer > 256 hits, station > 512 hits, > 64 trigger
+//                   (layer > 192 hits, station > 384 hits, > 64 trigger
 //                   triplets, or hits whose pruning bound is not finite).
 //                   Reads hits straight from global memory; pair pruning
 //                   only where it is proven (finite bounds).
@@ -33,10 +33,10 @@
 
 namespace jpsi {
 
-constexpr int kRMax = 8;                  // hits per lane per layer (warp path)
-constexpr int kLayerCap = 32 * kRMax;     // 256 hits per layer
-constexpr int kHCap = 512;                // hits per station tile
-constexpr int kQCap = 256;                // pair queue entries
+constexpr int kRMax = 6;                  // hits per lane per layer (warp path)
+constexpr int kLayerCap = 32 * kRMax;     // 192 hits per layer
+constexpr int kHCap = 384;                // hits per station tile
+constexpr int kQCap = 128;                // pair queue entries
 constexpr int kTCap = 64;                 // trigger triplets per event (CHAIN)
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -62,16 +62,16 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, d));
-    return v;
+// Warp min/max of non-NaN floats through the integer reduction unit: the map
+// below is strictly increasing on floats ordered by value (-0 < +0 aside,
+// which both reductions treat consistently).
+__device__ __forceinline__ int f2key(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
 }
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
-    return v;
-}
+__device__ __forceinline__ float key2f(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+__device__ __forceinline__ float warp_min(float v) { return key2f(__reduce_min_sync(kFull, f2key(v))); }
+__device__ __forceinline__ float warp_max(float v) { return key2f(__reduce_max_sync(kFull, f2key(v))); }
 
 // ------------------------------------------------------- event offsets
 
@@ -146,7 +146,8 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
         inv_w = __fdiv_rn((float)kNB, __fsub_rn(hi, lo));
         if (!isfinite(inv_w)) inv_w = 0.0f;
     }
-    t.bst[l][lane] = 0;
+    t.bst[l][2 * lane] = 0;
+    t.bst[l][2 * lane + 1] = 0;
     __syncwarp();
     int bin[kRMax], rank[kRMax];
 #pragma unroll
@@ -165,7 +166,9 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
             rank[r] = cur + before;
         }
     }
-    const int cnt = t.bst[l][lane];
+    // exclusive scan of the 64 bin counts, two per lane
+    const int c0 = t.bst[l][2 * lane], c1 = t.bst[l][2 * lane + 1];
+    const int cnt = c0 + c1;
     int incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -174,7 +177,8 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
     }
     const int total = __shfl_sync(kFull, incl, 31);
     __syncwarp();
-    t.bst[l][lane] = (uint16_t)(pbase + incl - cnt);
+    t.bst[l][2 * lane] = (uint16_t)(pbase + incl - cnt);
+    t.bst[l][2 * lane + 1] = (uint16_t)(pbase + incl - cnt + c0);
     if (lane == 31) t.bst[l][kNB] = (uint16_t)(pbase + total);
     __syncwarp();
 #pragma unroll
@@ -217,48 +221,57 @@ __device__ __forceinline__ void layer_range(const WarpTile& t, int l, float c, f
 // ---------------------------------------------------------- enumeration
 
 // Drains the pair queue: every (i, j) against the L2 hits of both bin windows.
+// The (pair, k) items of up to 32 pairs are spread evenly over the lanes (a
+// warp prefix sum over the window lengths; each lane finds the pair that owns
+// its item by a 5-step search over the lanes' exclusive sums).
 template <bool EMIT>
 __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn, bool collectT, int& nT,
-                      int32_t* rows, int limit, int& count) {
+                      int32_t* rows, int limit, int64_t unit, int& count) {
     const float bmax2 = t.meta[2].bmax;
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int q = q0 + lane;
-        const bool has = q < qn;
-        float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Pj = Pi;
-        int kb = 0, ke = 0, ii = 0, jj = 0;
-        float xi = 0.f, yi = 0.f, zi = 0.f, xj = 0.f, yj = 0.f, zj = 0.f;
-        if (has) {
-            const uint32_t en = t.queue[q];
-            Pi = t.P[en & 0xffffu];
-            Pj = t.P[en >> 16];
-            ii = __float_as_int(Pi.w);
-            jj = __float_as_int(Pj.w);
+        uint32_t en = 0;
+        int kb = 0, len = 0;
+        if (q < qn) {
+            en = t.queue[q];
+            const float4 Pi = t.P[en & 0xffffu], Pj = t.P[en >> 16];
             int a1, e1, a2, e2;
             layer_range(t, 2, Pi.x, __fadd_rn(Pi.z, bmax2), a1, e1);
             layer_range(t, 2, Pj.x, __fadd_rn(Pj.z, bmax2), a2, e2);
             kb = max(a1, a2);
-            ke = min(e1, e2);
-            xi = __ldg(j.x + base0 + ii);
-            yi = __ldg(j.y + base0 + ii);
-            zi = __ldg(j.z + base0 + ii);
-            xj = __ldg(j.x + base1 + jj);
-            yj = __ldg(j.y + base1 + jj);
-            zj = __ldg(j.z + base1 + jj);
+            len = max(min(e1, e2) - kb, 0);
         }
-        const int len = max(ke - kb, 0);
-        const int maxlen = __reduce_max_sync(kFull, len);
-        for (int tt = 0; tt < maxlen; ++tt) {
+        int incl = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        for (int it0 = 0; it0 < total; it0 += 32) {
+            const int it = it0 + lane;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, o + s);
+                if (ex <= it) o += s;
+            }
+            const uint32_t eo = __shfl_sync(kFull, en, o);
+            const int ko = __shfl_sync(kFull, kb, o) + (it - __shfl_sync(kFull, excl, o));
             bool ok = false;
             float mx = 0.f, my = 0.f;
-            int kk = 0;
-            if (tt < len) {
-                const float4 Pk = t.P[kb + tt];
+            int ii = 0, jj = 0, kk = 0;
+            if (it < total) {
+                const float4 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[ko];
                 if (pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) && pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
+                    ii = __float_as_int(Pi.w);
+                    jj = __float_as_int(Pj.w);
                     kk = __float_as_int(Pk.w);
-                    const float xs[3] = {xi, xj, __ldg(j.x + base2 + kk)};
-                    const float ys[3] = {yi, yj, __ldg(j.y + base2 + kk)};
-                    const float zs[3] = {zi, zj, __ldg(j.z + base2 + kk)};
+                    const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
+                    const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
+                    const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
                     ok = fit_pass(xs, ys, zs, c, mx, my);
                 }
             }
@@ -275,6 +288,18 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
                     if (ok && nT + rank < kTCap) t.T[nT + rank] = make_float2(mx, my);
                     nT += __popc(mask);
                 }
+                if (!EMIT && j.tscr) {  // record for the scatter pass
+                    unsigned long long b = 0;
+                    if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)__popc(mask));
+                    b = __shfl_sync(kFull, b, 0) + rank;
+                    if (ok && b < (unsigned long long)j.tscr_cap) {
+                        TripEntry en2;
+                        en2.unit = (int32_t)unit;
+                        en2.rank = count + rank;
+                        en2.ijk = (unsigned long long)ii | ((unsigned long long)jj << 21) | ((unsigned long long)kk << 42);
+                        j.tscr[b] = en2;
+                    }
+                }
                 count += __popc(mask);
             }
         }
@@ -285,7 +310,7 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
 // All passing triplets of the staged station (Sec. 3.2 steps 1-2).
 template <bool EMIT>
 __device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts& c, bool collectT, int& nT,
-                                 int32_t* rows, int limit) {
+                                 int32_t* rows, int limit, int64_t unit) {
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
     const int p0 = t.meta[0].pbase;
@@ -315,14 +340,14 @@ __device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
-                    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, count);
+                    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, unit, count);
                     qn = 0;
                 }
             }
         }
     }
     __syncwarp();
-    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, count);
+    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, unit, count);
     return count;
 }
 
@@ -408,7 +433,7 @@ __device__ void light_event_count(const Job& j, WarpTile& t, int lane, const Cut
             return;
         }
         const bool collect = chain && s == j.trig;
-        const int cnt = enumerate_station<false>(j, t, lane, c, collect, nT, nullptr, 0);
+        const int cnt = enumerate_station<false>(j, t, lane, c, collect, nT, nullptr, 0, e * S + s);
         if (collect) {
             if (nT > kTCap) {
                 to_generic(j, e, lane);
@@ -460,13 +485,13 @@ __device__ void light_event_emit(const Job& j, WarpTile& t, int lane, const Cuts
             return;
         }
         int nT = 0;
-        const int got = enumerate_station<true>(j, t, lane, c, false, nT, j.triplets + 3 * j.trip_off[u], cnt);
+        const int got = enumerate_station<true>(j, t, lane, c, false, nT, j.triplets + 3 * j.trip_off[u], cnt, u);
         if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
     }
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_light(const Job* __restrict__ djob, int persistent) {
+__global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, int persistent) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Job j = *djob;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -604,6 +629,22 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
                     float mx, my;
                     if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
                     ++local;
+                    if (!EMIT && j.tscr) {
+                        const int rk = atomicAdd(&s_count, 1);
+                        if (i >= kPackLimit || jx >= kPackLimit || k >= kPackLimit) {
+                            atomicOr(&j.ctrl->status, kStNoScratch);
+                        } else {
+                            const unsigned long long b = atomicAdd(&j.ctrl->scratch_n, 1ull);
+                            if (b < (unsigned long long)j.tscr_cap) {
+                                TripEntry en;
+                                en.unit = (int32_t)u;
+                                en.rank = rk;
+                                en.ijk = (unsigned long long)i | ((unsigned long long)jx << 21) |
+                                         ((unsigned long long)k << 42) | kFromGeneric;
+                                j.tscr[b] = en;
+                            }
+                        }
+                    }
                     if (EMIT) {
                         const int pos = atomicAdd(&s_count, 1);
                         if (pos < ulimit) {  // never past the unit's rows
@@ -616,7 +657,7 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
                     if (collect && road_global(j, soff, c, mx, my)) atomicAdd(&s_cand, 1);
                 }
             }
-            if (!EMIT && local) atomicAdd(&s_count, local);
+            if (!EMIT && !j.tscr && local) atomicAdd(&s_count, local);
             __syncthreads();
             if (threadIdx.x == 0) {
                 if (EMIT) {
@@ -752,6 +793,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Job* __restric
     }
 }
 
+// ------------------------------------------------------ triplet scatter
+
+// Moves each recorded triplet to its row trip_off[unit] + rank.  Entries of
+// events that moved from the warp path to the block path part-way are
+// dropped (the block path recorded the event again).
+__global__ void k_scatter(const Job* __restrict__ djob) {
+    const Job j = *djob;
+    const unsigned long long n = j.ctrl->scratch_n;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const TripEntry en = j.tscr[q];
+        const int64_t e = en.unit / j.S;
+        const bool from_generic = (en.ijk & kFromGeneric) != 0;
+        if ((j.ev_class[e] == 1) != from_generic) continue;
+        int32_t* r = j.triplets + 3 * (j.trip_off[en.unit] + en.rank);
+        r[0] = (int32_t)(en.ijk & 0x1fffff);
+        r[1] = (int32_t)((en.ijk >> 21) & 0x1fffff);
+        r[2] = (int32_t)((en.ijk >> 42) & 0x1fffff);
+    }
+}
+
 // ------------------------------------------------------------ launchers
 
 size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile); }
@@ -808,6 +870,11 @@ cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t
     k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
     k_scan_top<<<1, kScanThreads, 0, st>>>(djob);
     k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_scatter<<<lc.scan_blocks, 256, 0, st>>>(djob);
     return cudaGetLastError();
 }
 
