@@ -17,7 +17,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/jpsi.h"
+#include "jpsi.h"
 #include "jpsi_internal.h"
 
 using namespace jpsi;

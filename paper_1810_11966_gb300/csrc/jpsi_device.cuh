@@ -7,25 +7,29 @@
 // Both use __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn so that nothing is
 // contracted into an FMA and every step rounds to nearest in the order below.
 //
-// Pruning part (only skips work): per hit, s_u = u * fl(1/z) and a bound
-//     b = K * fl(1/z) + kappa * (|s_x| + |s_y|) + tau,
-//     K = sqrt(max C)(1 + 1e-4) + 1e-20 (rounded up), kappa = 2^-20, tau = 1e-37.
+// Pruning part (only skips work): per hit, s_u = u * r with r ~ 1/z from the
+// hardware reciprocal approximation (rcp.approx.ftz.f32; a relative error of
+// a few 2^-23 at most, used only for normal z in [2^-126, 2^126)), and a bound
+//     b = K * r + kappa * (|s_x| + |s_y|) + tau,
+//     K = sqrt(max C)(1 + 1e-4) + 1e-20 (rounded up), kappa = 2^-17, tau = 1e-37.
 // If a triplet passes P1 with slope m, each hit obeys
 //     |u_k/z_k - m| <= (|r_k|(1+2eps) + eps |m z_k|) / z_k,  |r_k| <= sqrt(C)(1+2eps) + 2^-74
 // (eps = 2^-24; the 2^-74 covers squares that underflow).  Subtracting the
-// relations of two hits and adding the rounding of s (<= 2.0001 eps |s|) gives
+// relations of two hits and adding the error of s (< 2^-20 |s|) gives
 //     |s_i - s_j| <= b_i (1 - 5e-5) + b_j (1 - 5e-5),
 // so the FP32 test |fl(s_i - s_j)| <= fl(b_i + b_j) never rejects a pair that
-// belongs to a passing triplet.  Hits with a non-finite coordinate cannot pass
-// P1 at all (Szz, Suz or a residual becomes Inf/NaN) and are dropped; hits with
-// finite coordinates but a non-finite s or b send their event to the
-// unpruned path.
+// belongs to a passing triplet (K's 1e-4 slack covers the error of r, kappa
+// the relative errors of s and eps |m|).  Hits with a non-finite coordinate
+// cannot pass P1 at all (Szz, Suz or a residual becomes Inf/NaN) and are
+// dropped; hits with finite coordinates but z outside [2^-126, 2^126) or a
+// non-finite s or b send their event to the unpruned path.
 #pragma once
 #include <cstdint>
 
 namespace jpsi {
 
-constexpr float kKappa = 9.5367431640625e-07f;  // 2^-20
+constexpr float kKappa = 7.62939453125e-06f;    // 2^-17
+constexpr float kPad = 9.5367431640625e-07f;     // 2^-20, query padding
 constexpr float kTau = 1e-37f;
 constexpr int kNB = 64;                          // slope bins per layer
 
@@ -92,27 +96,30 @@ struct HitPrep {
 __device__ __forceinline__ HitPrep hit_prep(float x, float y, float z, float K) {
     HitPrep h;
     h.zbad = z <= 0.0f;
-    h.live = isfinite(x) && isfinite(y) && isfinite(z);
-    const float iz = __frcp_rn(z);
+    h.live = (fabsf(x) < INFINITY) & (fabsf(y) < INFINITY) & (fabsf(z) < INFINITY);
+    float iz;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(z));
     h.sx = __fmul_rn(x, iz);
     h.sy = __fmul_rn(y, iz);
     h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, __fadd_rn(fabsf(h.sx), fabsf(h.sy)))), kTau);
-    h.wild = h.live && !(isfinite(h.sx) && isfinite(h.sy) && isfinite(h.b));
+    // b finite implies s_x, s_y finite (b >= kappa |s|)
+    h.wild = h.live & !((z >= 1.17549435e-38f) & (z < 8.50705917e+37f) & (h.b < INFINITY));
     return h;
 }
 
 // May hits i and j belong to one passing triplet?  (never false for such a pair)
 __device__ __forceinline__ bool pair_ok(float sxi, float syi, float bi, float sxj, float syj, float bj) {
     const float bb = __fadd_rn(bi, bj);
-    return (fabsf(__fsub_rn(sxi, sxj)) <= bb) && (fabsf(__fsub_rn(syi, syj)) <= bb);
+    return (fabsf(__fsub_rn(sxi, sxj)) <= bb) & (fabsf(__fsub_rn(syi, syj)) <= bb);
 }
 
 // May a hit pass the tube of trigger slope (mx, my)?  From tube_pass:
-// |s - m| <= b (1 - 5e-5) + 2^-21 |m| for a passing hit.
+// |s - m| <= b (1 - 5e-5) + 2^-21 |m| for a passing hit; the test allows
+// b + 2^-16 |m|.
 __device__ __forceinline__ bool tube_ok(float sx, float sy, float b, float mx, float my) {
     const float wx = __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx)));
     const float wy = __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my)));
-    return (fabsf(__fsub_rn(sx, mx)) <= wx) && (fabsf(__fsub_rn(sy, my)) <= wy);
+    return (fabsf(__fsub_rn(sx, mx)) <= wx) & (fabsf(__fsub_rn(sy, my)) <= wy);
 }
 
 // Slope bins of one layer: bin(v) = clamp(floor((v - lo) * inv_w), 0, NB-1),
@@ -127,7 +134,7 @@ __device__ __forceinline__ int slope_bin(float v, float lo, float inv_w) {
 // the half-width is padded by 2^-18 W + 2^-20 |c|, which exceeds the rounding
 // of c -/+ W'' (<= eps (|c| + W'')).
 __device__ __forceinline__ void query_bins(float c, float W, float lo, float inv_w, int& b0, int& b1) {
-    const float Wp = __fadd_rn(__fadd_rn(__fmul_rn(W, 1.000003814697265625f), __fmul_rn(kKappa, fabsf(c))), kTau);
+    const float Wp = __fadd_rn(__fadd_rn(__fmul_rn(W, 1.000003814697265625f), __fmul_rn(kPad, fabsf(c))), kTau);
     b0 = slope_bin(__fsub_rn(c, Wp), lo, inv_w);
     b1 = slope_bin(__fadd_rn(c, Wp), lo, inv_w);
 }

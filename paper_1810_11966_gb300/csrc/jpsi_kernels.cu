@@ -54,6 +54,7 @@ struct WarpTile {
     uint8_t alive[kTCap];
     uint16_t bst[3][kNB + 1];  // bin starts (tile positions) per layer
     LayerMeta meta[3];
+    uint32_t hist[kNB];        // bin counts of the layer being staged
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -70,6 +71,18 @@ __device__ __forceinline__ int f2key(float f) {
     return i >= 0 ? i : i ^ 0x7fffffff;
 }
 __device__ __forceinline__ float key2f(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+// Index of the lane whose exclusive prefix `excl` is the last one <= it
+// (excl non-decreasing over the lanes): binary lifting over shuffles.
+__device__ __forceinline__ int owner_lane(int excl, int it) {
+    int o = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int ex = __shfl_sync(kFull, excl, o + s);
+        o += (ex <= it) ? s : 0;
+    }
+    return o;
+}
+
 __device__ __forceinline__ float warp_min(float v) { return key2f(__reduce_min_sync(kFull, f2key(v))); }
 __device__ __forceinline__ float warp_max(float v) { return key2f(__reduce_max_sync(kFull, f2key(v))); }
 
@@ -109,31 +122,35 @@ __device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? t
 // ------------------------------------------------------------- staging
 
 // Stages one layer into the tile.  Returns 0, or 1 (z <= 0), or 2 (a hit
-// whose pruning bound is not finite).
+// whose pruning bound is not finite).  Hits are counted into slope bins with
+// shared-memory atomics (the order inside a bin is not fixed; results do not
+// depend on it) and written sorted by bin.
 __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32_t n, int32_t pbase, int lane,
                            int& nlive) {
     float sx[kRMax], sy[kRMax], bb[kRMax];
     bool lv[kRMax];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
+    t.hist[2 * lane] = 0;
+    t.hist[2 * lane + 1] = 0;
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         lv[r] = false;
         sx[r] = sy[r] = bb[r] = 0.0f;
-        const int h = lane + 32 * r;
-        if (32 * r < n && h < n) {
-            const HitPrep p = hit_prep(__ldg(j.x + base + h), __ldg(j.y + base + h), __ldg(j.z + base + h), j.K);
-            zbad |= p.zbad;
-            wild |= p.wild;
-            lv[r] = p.live && !p.wild;
+        if (32 * r < n) {  // warp-uniform
+            const int h = lane + 32 * r;
+            const bool in = h < n;
+            const int hc = in ? h : n - 1;  // clamped: loads stay inside the layer
+            const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
+            zbad |= in & p.zbad;
+            wild |= in & p.wild;
+            lv[r] = in & p.live & !p.wild;
             sx[r] = p.sx;
             sy[r] = p.sy;
             bb[r] = p.b;
-            if (lv[r]) {
-                lo = fminf(lo, p.sx);
-                hi = fmaxf(hi, p.sx);
-                bmax = fmaxf(bmax, p.b);
-            }
+            lo = lv[r] ? fminf(lo, p.sx) : lo;
+            hi = lv[r] ? fmaxf(hi, p.sx) : hi;
+            bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
         }
     }
     if (__any_sync(kFull, zbad)) return 1;
@@ -144,30 +161,22 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
     float inv_w = 0.0f;
     if (hi > lo) {
         inv_w = __fdiv_rn((float)kNB, __fsub_rn(hi, lo));
-        if (!isfinite(inv_w)) inv_w = 0.0f;
+        if (!(inv_w < INFINITY)) inv_w = 0.0f;
     }
-    t.bst[l][2 * lane] = 0;
-    t.bst[l][2 * lane + 1] = 0;
     __syncwarp();
     int bin[kRMax], rank[kRMax];
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         bin[r] = 0;
         rank[r] = 0;
-        if (32 * r < n) {
-            const int bn = lv[r] ? slope_bin(sx[r], lo, inv_w) : -1;
-            const unsigned peers = __match_any_sync(kFull, bn);
-            const int before = __popc(peers & lanemask_lt());
-            const int cur = lv[r] ? (int)t.bst[l][bn] : 0;
-            __syncwarp();
-            if (lv[r] && before == 0) t.bst[l][bn] = (uint16_t)(cur + __popc(peers));
-            __syncwarp();
-            bin[r] = bn;
-            rank[r] = cur + before;
+        if (32 * r < n && lv[r]) {
+            bin[r] = slope_bin(sx[r], lo, inv_w);
+            rank[r] = (int)atomicAdd(&t.hist[bin[r]], 1u);
         }
     }
+    __syncwarp();
     // exclusive scan of the 64 bin counts, two per lane
-    const int c0 = t.bst[l][2 * lane], c1 = t.bst[l][2 * lane + 1];
+    const int c0 = (int)t.hist[2 * lane], c1 = (int)t.hist[2 * lane + 1];
     const int cnt = c0 + c1;
     int incl = cnt;
 #pragma unroll
@@ -176,7 +185,6 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
         if (lane >= d) incl += v;
     }
     const int total = __shfl_sync(kFull, incl, 31);
-    __syncwarp();
     t.bst[l][2 * lane] = (uint16_t)(pbase + incl - cnt);
     t.bst[l][2 * lane + 1] = (uint16_t)(pbase + incl - cnt + c0);
     if (lane == 31) t.bst[l][kNB] = (uint16_t)(pbase + total);
@@ -250,22 +258,19 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
         }
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - len;
+        const int kshift = kb - excl;
         for (int it0 = 0; it0 < total; it0 += 32) {
             const int it = it0 + lane;
-            int o = 0;
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                const int ex = __shfl_sync(kFull, excl, o + s);
-                if (ex <= it) o += s;
-            }
+            const int o = owner_lane(excl, it);
             const uint32_t eo = __shfl_sync(kFull, en, o);
-            const int ko = __shfl_sync(kFull, kb, o) + (it - __shfl_sync(kFull, excl, o));
+            const int ko = __shfl_sync(kFull, kshift, o) + it;
             bool ok = false;
             float mx = 0.f, my = 0.f;
             int ii = 0, jj = 0, kk = 0;
-            if (it < total) {
-                const float4 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[ko];
-                if (pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) && pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
+            const bool in = it < total;
+            const float4 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[in ? ko : (int)(eo >> 16)];
+            if (in & pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) & pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
+                {
                     ii = __float_as_int(Pi.w);
                     jj = __float_as_int(Pj.w);
                     kk = __float_as_int(Pk.w);
@@ -307,7 +312,10 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
     __syncwarp();
 }
 
-// All passing triplets of the staged station (Sec. 3.2 steps 1-2).
+// All passing triplets of the staged station (Sec. 3.2 steps 1-2).  Rounds of
+// 32 L0 hits: each hit's L1 candidate window (slope bins) is spread over the
+// lanes, so every lane tests one candidate pair per step; pairs that may
+// belong to a passing triplet are queued and drained against L2.
 template <bool EMIT>
 __device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts& c, bool collectT, int& nT,
                                  int32_t* rows, int limit, int64_t unit) {
@@ -317,26 +325,31 @@ __device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts
     const float bmax1 = t.meta[1].bmax;
     int qn = 0, count = 0;
     for (int i0 = 0; i0 < n0; i0 += 32) {
-        const int pi = p0 + i0 + lane;
         const bool has = i0 + lane < n0;
-        float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
-        int jb = 0, je = 0;
-        if (has) {
-            Pi = t.P[pi];
-            layer_range(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
+        const float4 Pi = t.P[p0 + (has ? i0 + lane : 0)];
+        int jb, je;
+        layer_range(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
+        const int len = has ? je - jb : 0;
+        int incl = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
         }
-        const int len = je - jb;
-        const int maxlen = __reduce_max_sync(kFull, len);
-        for (int tt = 0; tt < maxlen; ++tt) {
-            bool pass = false;
-            const int pj = jb + tt;
-            if (tt < len) {
-                const float4 Pj = t.P[pj];
-                pass = pair_ok(Pi.x, Pi.y, Pi.z, Pj.x, Pj.y, Pj.z);
-            }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        const int shift = jb - excl;  // candidate position = shift(owner) + item
+        for (int it0 = 0; it0 < total; it0 += 32) {
+            const int it = it0 + lane;
+            const int o = owner_lane(excl, it);
+            const int pj = __shfl_sync(kFull, shift, o) + it;
+            const bool in = it < total;
+            const float4 Po = t.P[p0 + i0 + o];
+            const float4 Pj = t.P[in ? pj : p0];
+            const bool pass = in & pair_ok(Po.x, Po.y, Po.z, Pj.x, Pj.y, Pj.z);
             const unsigned mask = __ballot_sync(kFull, pass);
             if (mask) {
-                if (pass) t.queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)pi | ((uint32_t)pj << 16);
+                if (pass) t.queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
