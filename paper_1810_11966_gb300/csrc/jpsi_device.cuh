@@ -31,7 +31,6 @@ namespace jpsi {
 constexpr float kKappa = 7.62939453125e-06f;    // 2^-17
 constexpr float kPad = 9.5367431640625e-07f;     // 2^-20, query padding
 constexpr float kTau = 1e-37f;
-constexpr int kNB = 64;                          // slope bins per layer
 
 struct Cuts {
     float cx, cy;  // thresholds on S_x, S_y: fl32(ndf * t)
@@ -125,18 +124,20 @@ __device__ __forceinline__ bool tube_ok(float sx, float sy, float b, float mx, f
 // Slope bins of one layer: bin(v) = clamp(floor((v - lo) * inv_w), 0, NB-1),
 // non-decreasing in v (each step is a monotone rounding), so a value range
 // maps to a contiguous bin range.
+template <int NB>
 __device__ __forceinline__ int slope_bin(float v, float lo, float inv_w) {
     const float t = floorf(__fmul_rn(__fsub_rn(v, lo), inv_w));
-    return (int)fminf(fmaxf(t, 0.0f), (float)(kNB - 1));  // NaN -> 0 (only when inv_w = 0)
+    return (int)fminf(fmaxf(t, 0.0f), (float)(NB - 1));  // NaN -> 0 (only when inv_w = 0)
 }
 
 // Bins that contain every stored value v with |v - c| <= W (1 + 2^-20):
 // the half-width is padded by 2^-18 W + 2^-20 |c|, which exceeds the rounding
 // of c -/+ W'' (<= eps (|c| + W'')).
+template <int NB>
 __device__ __forceinline__ void query_bins(float c, float W, float lo, float inv_w, int& b0, int& b1) {
     const float Wp = __fadd_rn(__fadd_rn(__fmul_rn(W, 1.000003814697265625f), __fmul_rn(kPad, fabsf(c))), kTau);
-    b0 = slope_bin(__fsub_rn(c, Wp), lo, inv_w);
-    b1 = slope_bin(__fadd_rn(c, Wp), lo, inv_w);
+    b0 = slope_bin<NB>(__fsub_rn(c, Wp), lo, inv_w);
+    b1 = slope_bin<NB>(__fadd_rn(c, Wp), lo, inv_w);
 }
 
 }  // namespace jpsi

@@ -1,28 +1,34 @@
 // Kernels of the J/psi first-level selection (arXiv:1810.11966, Sec. 3.2) on
-// sm_103a.  Work unit: one event (all of its stations).
+// sm_103a.  Work unit: one event (all of its stations).  Three paths, chosen
+// per event, give bit-identical results:
 //
-//   k_light_count   one warp per event.  Each station's hits are staged from
-//                   HBM (coalesced loads, registers) into a per-warp shared
-//                   tile sorted into slope bins; pairs (L0, L1) that may
-//                   belong to a passing triplet go to a pair queue through
-//                   ballot/popc compaction; the queue is drained against the
-//                   L2 hits of the pair's bin window and every surviving
-//                   triple gets the exact FP32 fit (P1).  CHAIN mode keeps the
-//                   trigger triplets' slopes in the tile and searches the
-//                   other stations' tiles for compatible triplets (P2).
-//   k_generic       one block per event for events the warp tile cannot hold
-//                   (layer > 192 hits, station > 384 hits, > 64 trigger
-//                   triplets, or hits whose pruning bound is not finite).
-//                   Reads hits straight from global memory; pair pruning
-//                   only where it is proven (finite bounds).
-//   k_accept        accept bits from track counts (ballot per 32 events).
-//   k_scan*         exclusive scan of per-unit counts into int64 trip_off.
-//   *_emit          second pass when triplet lists are requested: the same
-//                   enumeration writes rows at trip_off[unit].
+//   k_light    one warp per event.  Each station's hits are staged from HBM
+//              (coalesced loads into registers) into a per-warp shared tile
+//              sorted into 64 slope bins per layer.  Pairs (L0, L1) whose
+//              slopes are close enough to belong to a passing triplet are
+//              found with the candidate windows of 32 L0 hits spread evenly
+//              over the lanes, compacted into a pair queue with ballot/popc,
+//              and drained against the L2 hits of both bin windows; every
+//              surviving triple gets the exact FP32 fit (P1).  CHAIN mode
+//              keeps the passing trigger triplets' slopes in the tile and
+//              searches the other stations' tiles for compatible triplets
+//              (P2).  Limits: 192 hits per layer, 384 per station, 64
+//              passing trigger triplets.
+//   k_heavy    one 8-warp block per event for larger events: the same
+//              enumeration over a block tile (2048 hits per layer, 6144 per
+//              station, 256 slope bins), warps splitting the L0 rounds,
+//              trigger slopes in a per-block global list.
+//   k_generic  one block per event, unpruned where the pruning bound is not
+//              finite (extreme coordinates) and no size limit: reads hits
+//              straight from global memory.
+//   k_accept   accept bits from track counts (ballot per 32 events).
+//   k_scan*    exclusive scan of per-unit counts into int64 trip_off.
+//   k_scatter  moves the triplets recorded by the counting pass to their rows
+//              trip_off[unit] + rank; when the record overflowed, the emit
+//              variants of the three kernels re-enumerate instead.
 //
-// Results never depend on the path an event takes: pruning only skips triples
-// that provably fail P1 (see jpsi_device.cuh), and P1/P2 are the same
-// correctly rounded FP32 expressions everywhere.
+// Pruning only skips triples that provably fail P1 (see jpsi_device.cuh), and
+// P1/P2 are the same correctly rounded FP32 expressions everywhere.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,12 +39,23 @@
 
 namespace jpsi {
 
-constexpr int kRMax = 6;                  // hits per lane per layer (warp path)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kQCap = 128;                // pair queue entries per warp
+
+// warp path
+constexpr int kRMax = 6;                  // hits per lane per layer
 constexpr int kLayerCap = 32 * kRMax;     // 192 hits per layer
 constexpr int kHCap = 384;                // hits per station tile
-constexpr int kQCap = 128;                // pair queue entries
-constexpr int kTCap = 64;                 // trigger triplets per event (CHAIN)
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTCap = 64;                 // passing trigger triplets per event (CHAIN)
+constexpr int kNBL = 64;                  // slope bins per layer
+
+// block-tile path
+constexpr int kHThreads = 256;
+constexpr int kHWarps = kHThreads / 32;
+constexpr int kHRMax = 8;                         // hits per thread per layer
+constexpr int kHLayerCap = kHThreads * kHRMax;    // 2048 hits per layer
+constexpr int kHHCap = 6144;                      // hits per station tile
+constexpr int kNBH = 256;                         // slope bins per layer
 
 struct LayerMeta {
     float lo, inv_w, bmax;
@@ -47,14 +64,37 @@ struct LayerMeta {
     int32_t nlive;  // stored hits (finite coordinates)
 };
 
+// One station staged in shared memory: hits (s_x, s_y, b, layer-local index
+// as int bits) sorted by slope bin, bin starts and per-layer metadata.
+template <int NB>
+struct TileView {
+    float4* P;
+    uint16_t* bst;  // [3][NB + 1] tile positions
+    LayerMeta* meta;
+    __device__ __forceinline__ int bin_start(int l, int b) const { return bst[l * (NB + 1) + b]; }
+};
+
 struct WarpTile {
-    float4 P[kHCap];           // s_x, s_y, b, layer-local hit index (int bits), sorted by slope bin
-    uint32_t queue[kQCap];     // tile positions (p_i | p_j << 16)
-    float2 T[kTCap];           // trigger triplet slopes
+    float4 P[kHCap];
+    uint32_t queue[kQCap];
+    float2 T[kTCap];            // trigger triplet slopes
     uint8_t alive[kTCap];
-    uint16_t bst[3][kNB + 1];  // bin starts (tile positions) per layer
+    uint16_t bst[3 * (kNBL + 1)];
     LayerMeta meta[3];
-    uint32_t hist[kNB];        // bin counts of the layer being staged
+    uint32_t hist[kNBL];        // bin counts of the layer being staged
+};
+
+struct HeavySmem {
+    float4 P[kHHCap];
+    uint32_t queue[kHWarps][kQCap];
+    uint16_t bst[3 * (kNBH + 1)];
+    LayerMeta meta[3];
+    uint32_t hist[kNBH];
+    int32_t off[3 * kMaxStations + 1];
+    int32_t wsum[kHWarps];
+    int red_i[kHWarps][2];
+    float red_f[kHWarps][3];
+    int s_gi, s_rank, s_nT, s_cand;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -63,14 +103,25 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Warp min/max of non-NaN floats through the integer reduction unit: the map
-// below is strictly increasing on floats ordered by value (-0 < +0 aside,
-// which both reductions treat consistently).
+// Min/max of non-NaN floats through the integer reduction unit: the map is
+// strictly increasing on floats ordered by value.
 __device__ __forceinline__ int f2key(float f) {
     const int i = __float_as_int(f);
     return i >= 0 ? i : i ^ 0x7fffffff;
 }
 __device__ __forceinline__ float key2f(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+__device__ __forceinline__ float warp_min(float v) { return key2f(__reduce_min_sync(kFull, f2key(v))); }
+__device__ __forceinline__ float warp_max(float v) { return key2f(__reduce_max_sync(kFull, f2key(v))); }
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
 // Index of the lane whose exclusive prefix `excl` is the last one <= it
 // (excl non-decreasing over the lanes): binary lifting over shuffles.
 __device__ __forceinline__ int owner_lane(int excl, int it) {
@@ -83,8 +134,7 @@ __device__ __forceinline__ int owner_lane(int excl, int it) {
     return o;
 }
 
-__device__ __forceinline__ float warp_min(float v) { return key2f(__reduce_min_sync(kFull, f2key(v))); }
-__device__ __forceinline__ float warp_max(float v) { return key2f(__reduce_max_sync(kFull, f2key(v))); }
+__device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? trig : (si - 1 < trig ? si - 1 : si); }
 
 // ------------------------------------------------------- event offsets
 
@@ -117,41 +167,41 @@ __device__ bool warp_load_offsets(const Job& j, int64_t e, int lane, EvOff& o) {
     return !__any_sync(kFull, bad);
 }
 
-__device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? trig : (si - 1 < trig ? si - 1 : si); }
+// ------------------------------------------------------- warp staging
 
-// ------------------------------------------------------------- staging
-
-// Stages one layer into the tile.  Returns 0, or 1 (z <= 0), or 2 (a hit
-// whose pruning bound is not finite).  Hits are counted into slope bins with
-// shared-memory atomics (the order inside a bin is not fixed; results do not
-// depend on it) and written sorted by bin.
-__device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32_t n, int32_t pbase, int lane,
-                           int& nlive) {
+// Stages one layer into the warp tile.  Returns 0, or 1 (z <= 0), or 2 (a
+// hit whose pruning bound is not finite).  Hits are counted into slope bins
+// with shared-memory atomics (the order inside a bin is not fixed; results
+// do not depend on it) and written sorted by bin.
+__device__ int stage_layer_warp(const Job& j, WarpTile& w, int l, int32_t base, int32_t n, int32_t pbase, int lane,
+                                int& nlive) {
     float sx[kRMax], sy[kRMax], bb[kRMax];
     bool lv[kRMax];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
-    t.hist[2 * lane] = 0;
-    t.hist[2 * lane + 1] = 0;
+    w.hist[2 * lane] = 0;
+    w.hist[2 * lane + 1] = 0;
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         lv[r] = false;
         sx[r] = sy[r] = bb[r] = 0.0f;
-        if (32 * r < n) {  // warp-uniform
-            const int h = lane + 32 * r;
-            const bool in = h < n;
-            const int hc = in ? h : n - 1;  // clamped: loads stay inside the layer
-            const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
-            zbad |= in & p.zbad;
-            wild |= in & p.wild;
-            lv[r] = in & p.live & !p.wild;
-            sx[r] = p.sx;
-            sy[r] = p.sy;
-            bb[r] = p.b;
-            lo = lv[r] ? fminf(lo, p.sx) : lo;
-            hi = lv[r] ? fmaxf(hi, p.sx) : hi;
-            bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
-        }
+    }
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        if (32 * r >= n) break;  // warp-uniform
+        const int h = lane + 32 * r;
+        const bool in = h < n;
+        const int hc = in ? h : n - 1;  // clamped: loads stay inside the layer
+        const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
+        zbad |= in & p.zbad;
+        wild |= in & p.wild;
+        lv[r] = in & p.live & !p.wild;
+        sx[r] = p.sx;
+        sy[r] = p.sy;
+        bb[r] = p.b;
+        lo = lv[r] ? fminf(lo, p.sx) : lo;
+        hi = lv[r] ? fmaxf(hi, p.sx) : hi;
+        bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
     }
     if (__any_sync(kFull, zbad)) return 1;
     if (__any_sync(kFull, wild)) return 2;
@@ -160,7 +210,7 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
     bmax = warp_max(bmax);
     float inv_w = 0.0f;
     if (hi > lo) {
-        inv_w = __fdiv_rn((float)kNB, __fsub_rn(hi, lo));
+        inv_w = __fdiv_rn((float)kNBL, __fsub_rn(hi, lo));
         if (!(inv_w < INFINITY)) inv_w = 0.0f;
     }
     __syncwarp();
@@ -169,29 +219,31 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
     for (int r = 0; r < kRMax; ++r) {
         bin[r] = 0;
         rank[r] = 0;
-        if (32 * r < n && lv[r]) {
-            bin[r] = slope_bin(sx[r], lo, inv_w);
-            rank[r] = (int)atomicAdd(&t.hist[bin[r]], 1u);
+    }
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        if (32 * r >= n) break;
+        if (lv[r]) {
+            bin[r] = slope_bin<kNBL>(sx[r], lo, inv_w);
+            rank[r] = (int)atomicAdd(&w.hist[bin[r]], 1u);
         }
     }
     __syncwarp();
     // exclusive scan of the 64 bin counts, two per lane
-    const int c0 = (int)t.hist[2 * lane], c1 = (int)t.hist[2 * lane + 1];
+    const int c0 = (int)w.hist[2 * lane], c1 = (int)w.hist[2 * lane + 1];
     const int cnt = c0 + c1;
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += v;
-    }
+    const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    t.bst[l][2 * lane] = (uint16_t)(pbase + incl - cnt);
-    t.bst[l][2 * lane + 1] = (uint16_t)(pbase + incl - cnt + c0);
-    if (lane == 31) t.bst[l][kNB] = (uint16_t)(pbase + total);
+    uint16_t* bst = w.bst + l * (kNBL + 1);
+    bst[2 * lane] = (uint16_t)(pbase + incl - cnt);
+    bst[2 * lane + 1] = (uint16_t)(pbase + incl - cnt + c0);
+    if (lane == 31) bst[kNBL] = (uint16_t)(pbase + total);
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r)
-        if (lv[r]) t.P[t.bst[l][bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(lane + 32 * r));
+    for (int r = 0; r < kRMax; ++r) {
+        if (32 * r >= n) break;
+        if (lv[r]) w.P[bst[bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(lane + 32 * r));
+    }
     if (lane == 0) {
         LayerMeta m;
         m.lo = lo;
@@ -200,41 +252,165 @@ __device__ int stage_layer(const Job& j, WarpTile& t, int l, int32_t base, int32
         m.base = base;
         m.pbase = pbase;
         m.nlive = total;
-        t.meta[l] = m;
+        w.meta[l] = m;
     }
     __syncwarp();
     nlive = total;
     return 0;
 }
 
-__device__ int stage_station(const Job& j, WarpTile& t, int lane, const EvOff& o, int s) {
+__device__ int stage_station_warp(const Job& j, WarpTile& w, int lane, const EvOff& o, int s) {
     int pbase = 0;
     for (int l = 0; l < 3; ++l) {
         const int32_t b = off_get(o, s * 3 + l), e = off_get(o, s * 3 + l + 1);
         int nl = 0;
-        const int st = stage_layer(j, t, l, b, e - b, pbase, lane, nl);
+        const int st = stage_layer_warp(j, w, l, b, e - b, pbase, lane, nl);
         if (st) return st;
         pbase += nl;
     }
     return 0;
 }
 
-__device__ __forceinline__ void layer_range(const WarpTile& t, int l, float c, float W, int& a, int& e) {
+// ------------------------------------------------------ block staging
+
+// Block version of the staging for the block-tile path (256 threads).
+__device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t base, int32_t n, int32_t pbase,
+                                 int& nlive) {
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    float sx[kHRMax], sy[kHRMax], bb[kHRMax];
+    bool lv[kHRMax];
+    float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
+    bool zbad = false, wild = false;
+    sm.hist[tid] = 0;
+#pragma unroll
+    for (int r = 0; r < kHRMax; ++r) {
+        lv[r] = false;
+        sx[r] = sy[r] = bb[r] = 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < kHRMax; ++r) {
+        if (kHThreads * r >= n) break;  // block-uniform
+        const int h = tid + kHThreads * r;
+        const bool in = h < n;
+        const int hc = in ? h : n - 1;
+        const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
+        zbad |= in & p.zbad;
+        wild |= in & p.wild;
+        lv[r] = in & p.live & !p.wild;
+        sx[r] = p.sx;
+        sy[r] = p.sy;
+        bb[r] = p.b;
+        lo = lv[r] ? fminf(lo, p.sx) : lo;
+        hi = lv[r] ? fmaxf(hi, p.sx) : hi;
+        bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    bmax = warp_max(bmax);
+    const int fz = __any_sync(kFull, zbad), fw = __any_sync(kFull, wild);
+    if (lane == 0) {
+        sm.red_f[wp][0] = lo;
+        sm.red_f[wp][1] = hi;
+        sm.red_f[wp][2] = bmax;
+        sm.red_i[wp][0] = fz;
+        sm.red_i[wp][1] = fw;
+    }
+    __syncthreads();
+    int anyz = 0, anyw = 0;
+#pragma unroll
+    for (int q = 0; q < kHWarps; ++q) {
+        lo = fminf(lo, sm.red_f[q][0]);
+        hi = fmaxf(hi, sm.red_f[q][1]);
+        bmax = fmaxf(bmax, sm.red_f[q][2]);
+        anyz |= sm.red_i[q][0];
+        anyw |= sm.red_i[q][1];
+    }
+    __syncthreads();
+    if (anyz) return 1;
+    if (anyw) return 2;
+    float inv_w = 0.0f;
+    if (hi > lo) {
+        inv_w = __fdiv_rn((float)kNBH, __fsub_rn(hi, lo));
+        if (!(inv_w < INFINITY)) inv_w = 0.0f;
+    }
+    int bin[kHRMax], rank[kHRMax];
+#pragma unroll
+    for (int r = 0; r < kHRMax; ++r) {
+        bin[r] = 0;
+        rank[r] = 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kHRMax; ++r) {
+        if (kHThreads * r >= n) break;
+        if (lv[r]) {
+            bin[r] = slope_bin<kNBH>(sx[r], lo, inv_w);
+            rank[r] = (int)atomicAdd(&sm.hist[bin[r]], 1u);
+        }
+    }
+    __syncthreads();
+    // block exclusive scan of the 256 bin counts (one per thread)
+    const int cnt = (int)sm.hist[tid];
+    const int incl = warp_incl_scan(cnt, lane);
+    if (lane == 31) sm.wsum[wp] = incl;
+    __syncthreads();
+    int woff = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kHWarps; ++q) {
+        woff += q < wp ? sm.wsum[q] : 0;
+        total += sm.wsum[q];
+    }
+    uint16_t* bst = sm.bst + l * (kNBH + 1);
+    bst[tid] = (uint16_t)(pbase + woff + incl - cnt);
+    if (tid == kHThreads - 1) bst[kNBH] = (uint16_t)(pbase + total);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kHRMax; ++r) {
+        if (kHThreads * r >= n) break;
+        if (lv[r]) sm.P[bst[bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(tid + kHThreads * r));
+    }
+    if (tid == 0) {
+        LayerMeta m;
+        m.lo = lo;
+        m.inv_w = inv_w;
+        m.bmax = bmax;
+        m.base = base;
+        m.pbase = pbase;
+        m.nlive = total;
+        sm.meta[l] = m;
+    }
+    __syncthreads();
+    nlive = total;
+    return 0;
+}
+
+template <int NB>
+__device__ __forceinline__ void layer_range(const TileView<NB>& t, int l, float c, float W, int& a, int& e) {
     int b0, b1;
-    query_bins(c, W, t.meta[l].lo, t.meta[l].inv_w, b0, b1);
-    a = t.bst[l][b0];
-    e = t.bst[l][b1 + 1];
+    query_bins<NB>(c, W, t.meta[l].lo, t.meta[l].inv_w, b0, b1);
+    a = t.bin_start(l, b0);
+    e = t.bin_start(l, b1 + 1);
 }
 
 // ---------------------------------------------------------- enumeration
 
-// Drains the pair queue: every (i, j) against the L2 hits of both bin windows.
+// Where passing trigger triplets' slopes go (CHAIN mode, trigger station).
+// Warp path: a warp-local count; block path: a block-shared counter.
+struct TSink {
+    bool on;
+    float2* T;
+    int cap;
+    int* sh_n;  // block-shared counter, or null
+    int n;      // warp-local counter when sh_n is null
+};
+
+// Drains a pair queue: every (i, j) against the L2 hits of both bin windows.
 // The (pair, k) items of up to 32 pairs are spread evenly over the lanes (a
-// warp prefix sum over the window lengths; each lane finds the pair that owns
-// its item by a 5-step search over the lanes' exclusive sums).
-template <bool EMIT>
-__device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn, bool collectT, int& nT,
-                      int32_t* rows, int limit, int64_t unit, int& count) {
+// warp prefix sum over the window lengths; each lane finds the pair owning its
+// item by binary lifting).  Passing triplets get a rank inside their unit:
+// warp-local on the warp path, from a block-shared counter on the block path.
+template <bool EMIT, int NB>
+__device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
+                      TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count) {
     const float bmax2 = t.meta[2].bmax;
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int q0 = 0; q0 < qn; q0 += 32) {
@@ -242,20 +418,15 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
         uint32_t en = 0;
         int kb = 0, len = 0;
         if (q < qn) {
-            en = t.queue[q];
+            en = queue[q];
             const float4 Pi = t.P[en & 0xffffu], Pj = t.P[en >> 16];
             int a1, e1, a2, e2;
-            layer_range(t, 2, Pi.x, __fadd_rn(Pi.z, bmax2), a1, e1);
-            layer_range(t, 2, Pj.x, __fadd_rn(Pj.z, bmax2), a2, e2);
+            layer_range<NB>(t, 2, Pi.x, __fadd_rn(Pi.z, bmax2), a1, e1);
+            layer_range<NB>(t, 2, Pj.x, __fadd_rn(Pj.z, bmax2), a2, e2);
             kb = max(a1, a2);
             len = max(min(e1, e2) - kb, 0);
         }
-        int incl = len;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, d);
-            if (lane >= d) incl += v;
-        }
+        const int incl = warp_incl_scan(len, lane);
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - len;
         const int kshift = kb - excl;
@@ -270,72 +441,81 @@ __device__ void drain(const Job& j, WarpTile& t, int lane, const Cuts& c, int qn
             const bool in = it < total;
             const float4 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[in ? ko : (int)(eo >> 16)];
             if (in & pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) & pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
-                {
-                    ii = __float_as_int(Pi.w);
-                    jj = __float_as_int(Pj.w);
-                    kk = __float_as_int(Pk.w);
-                    const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
-                    const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
-                    const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
-                    ok = fit_pass(xs, ys, zs, c, mx, my);
-                }
+                ii = __float_as_int(Pi.w);
+                jj = __float_as_int(Pj.w);
+                kk = __float_as_int(Pk.w);
+                const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
+                const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
+                const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
+                ok = fit_pass(xs, ys, zs, c, mx, my);
             }
             const unsigned mask = __ballot_sync(kFull, ok);
             if (mask) {
-                const int rank = __popc(mask & lanemask_lt());
-                if (EMIT && ok && count + rank < limit) {  // never past the unit's rows
-                    int32_t* r = rows + 3 * (int64_t)(count + rank);
+                const int rk = __popc(mask & lanemask_lt()), np = __popc(mask);
+                int base = count;
+                if (sh_rank) {
+                    int b = 0;
+                    if (lane == 0) b = atomicAdd(sh_rank, np);
+                    base = __shfl_sync(kFull, b, 0);
+                }
+                if (EMIT && ok && base + rk < limit) {  // never past the unit's rows
+                    int32_t* r = rows + 3 * (int64_t)(base + rk);
                     r[0] = ii;
                     r[1] = jj;
                     r[2] = kk;
                 }
-                if (collectT) {
-                    if (ok && nT + rank < kTCap) t.T[nT + rank] = make_float2(mx, my);
-                    nT += __popc(mask);
+                if (ts.on) {
+                    int tb = ts.n;
+                    if (ts.sh_n) {
+                        int b = 0;
+                        if (lane == 0) b = atomicAdd(ts.sh_n, np);
+                        tb = __shfl_sync(kFull, b, 0);
+                    } else {
+                        ts.n += np;
+                    }
+                    if (ok && tb + rk < ts.cap) ts.T[tb + rk] = make_float2(mx, my);
                 }
                 if (!EMIT && j.tscr) {  // record for the scatter pass
                     unsigned long long b = 0;
-                    if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)__popc(mask));
-                    b = __shfl_sync(kFull, b, 0) + rank;
+                    if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)np);
+                    b = __shfl_sync(kFull, b, 0) + rk;
                     if (ok && b < (unsigned long long)j.tscr_cap) {
-                        TripEntry en2;
-                        en2.unit = (int32_t)unit;
-                        en2.rank = count + rank;
-                        en2.ijk = (unsigned long long)ii | ((unsigned long long)jj << 21) | ((unsigned long long)kk << 42);
-                        j.tscr[b] = en2;
+                        TripEntry te;
+                        te.unit = (int32_t)unit;
+                        te.rank = base + rk;
+                        te.ijk = (unsigned long long)ii | ((unsigned long long)jj << 20) |
+                                 ((unsigned long long)kk << 40) | ((unsigned long long)tag << kTagShift);
+                        j.tscr[b] = te;
                     }
                 }
-                count += __popc(mask);
+                count += np;
             }
         }
     }
     __syncwarp();
 }
 
-// All passing triplets of the staged station (Sec. 3.2 steps 1-2).  Rounds of
-// 32 L0 hits: each hit's L1 candidate window (slope bins) is spread over the
-// lanes, so every lane tests one candidate pair per step; pairs that may
-// belong to a passing triplet are queued and drained against L2.
-template <bool EMIT>
-__device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts& c, bool collectT, int& nT,
-                                 int32_t* rows, int limit, int64_t unit) {
+// All passing triplets of the staged station (Sec. 3.2 steps 1-2) found by
+// this warp: rounds of 32 L0 hits (rounds warp, warp + nwarps, ...), each
+// hit's L1 candidate window (slope bins) spread over the lanes so every lane
+// tests one candidate pair per step; pairs that may belong to a passing
+// triplet are queued and drained against L2.
+template <bool EMIT, int NB>
+__device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue, int lane, const Cuts& c,
+                            TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int warp,
+                            int nwarps) {
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
     const int p0 = t.meta[0].pbase;
     const float bmax1 = t.meta[1].bmax;
     int qn = 0, count = 0;
-    for (int i0 = 0; i0 < n0; i0 += 32) {
+    for (int i0 = 32 * warp; i0 < n0; i0 += 32 * nwarps) {
         const bool has = i0 + lane < n0;
         const float4 Pi = t.P[p0 + (has ? i0 + lane : 0)];
         int jb, je;
-        layer_range(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
+        layer_range<NB>(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
         const int len = has ? je - jb : 0;
-        int incl = len;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, d);
-            if (lane >= d) incl += v;
-        }
+        const int incl = warp_incl_scan(len, lane);
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - len;
         const int shift = jb - excl;  // candidate position = shift(owner) + item
@@ -349,28 +529,29 @@ __device__ int enumerate_station(const Job& j, WarpTile& t, int lane, const Cuts
             const bool pass = in & pair_ok(Po.x, Po.y, Po.z, Pj.x, Pj.y, Pj.z);
             const unsigned mask = __ballot_sync(kFull, pass);
             if (mask) {
-                if (pass) t.queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
+                if (pass) queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
-                    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, unit, count);
+                    drain<EMIT, NB>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
                     qn = 0;
                 }
             }
         }
     }
     __syncwarp();
-    drain<EMIT>(j, t, lane, c, qn, collectT, nT, rows, limit, unit, count);
+    drain<EMIT, NB>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
     return count;
 }
 
-// Does station (staged in the tile) hold a passing triplet compatible with
-// the trigger slopes (mx, my)?  Per-lane search through the slope bins.
-__device__ bool road(const Job& j, const WarpTile& t, const Cuts& c, float mx, float my) {
+// Does the staged station hold a passing triplet compatible with the
+// trigger slopes (mx, my)?  Per-thread search through the slope bins.
+template <int NB>
+__device__ bool road(const Job& j, const TileView<NB>& t, const Cuts& c, float mx, float my) {
     int a[3], e[3];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-        layer_range(t, l, mx, __fadd_rn(t.meta[l].bmax, __fmul_rn(2.0f * kKappa, fabsf(mx))), a[l], e[l]);
+        layer_range<NB>(t, l, mx, __fadd_rn(t.meta[l].bmax, __fmul_rn(2.0f * kKappa, fabsf(mx))), a[l], e[l]);
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int p0 = a[0]; p0 < e[0]; ++p0) {
         const float4 P0 = t.P[p0];
@@ -399,21 +580,26 @@ __device__ bool road(const Job& j, const WarpTile& t, const Cuts& c, float mx, f
     return false;
 }
 
-__device__ __forceinline__ void to_generic(const Job& j, int64_t e, int lane) {
-    if (lane == 0) {
-        j.ev_class[e] = 1;
+// ------------------------------------------------------------ warp path
+
+__device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls) {
+    j.ev_class[e] = cls;
+    if (cls == kClsHeavy) {
+        const int gi = atomicAdd(&j.ctrl->n_heavy, 1);
+        j.hlist[gi] = (int32_t)e;
+    } else {
         const int gi = atomicAdd(&j.ctrl->n_generic, 1);
         j.glist[gi] = (int32_t)e;
     }
 }
 
-__device__ void light_event_count(const Job& j, WarpTile& t, int lane, const Cuts& c, int64_t e) {
+__device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cuts& c, int64_t e) {
     EvOff o;
     const int S = j.S;
     if (!warp_load_offsets(j, e, lane, o)) {
         if (lane == 0) {
             atomicOr(&j.ctrl->status, kStInvalid);
-            j.ev_class[e] = 2;
+            j.ev_class[e] = kClsInvalid;
         }
         return;
     }
@@ -427,41 +613,45 @@ __device__ void light_event_count(const Job& j, WarpTile& t, int lane, const Cut
         if (o1 - o0 > kLayerCap || o2 - o1 > kLayerCap || o3 - o2 > kLayerCap || o3 - o0 > kHCap) fits = false;
     }
     if (!fits) {
-        to_generic(j, e, lane);
+        if (lane == 0) push_event(j, e, kClsHeavy);
         return;
     }
-    int nT = 0, trig_count = 0;
+    const TileView<kNBL> t{w.P, w.bst, w.meta};
+    TSink ts{false, w.T, kTCap, nullptr, 0};
+    int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
-        const int st = stage_station(j, t, lane, o, s);
+        const int st = stage_station_warp(j, w, lane, o, s);
         if (st == 1) {
             if (lane == 0) {
                 atomicOr(&j.ctrl->status, kStInvalid);
-                j.ev_class[e] = 2;
+                j.ev_class[e] = kClsInvalid;
             }
             return;
         }
         if (st == 2) {
-            to_generic(j, e, lane);
+            if (lane == 0) push_event(j, e, kClsGeneric);
             return;
         }
-        const bool collect = chain && s == j.trig;
-        const int cnt = enumerate_station<false>(j, t, lane, c, collect, nT, nullptr, 0, e * S + s);
-        if (collect) {
-            if (nT > kTCap) {
-                to_generic(j, e, lane);
+        ts.on = chain && s == j.trig;
+        const int cnt = enum_station<false, kNBL>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr,
+                                                  kClsLight, 0, 1);
+        if (ts.on) {
+            if (ts.n > kTCap) {
+                if (lane == 0) push_event(j, e, kClsHeavy);
                 return;
             }
-            for (int i = lane; i < nT; i += 32) t.alive[i] = 1;
+            for (int i = lane; i < ts.n; i += 32) w.alive[i] = 1;
             __syncwarp();
+            ts.on = false;
         }
         if (s == j.trig) trig_count = cnt;
         if (lane == 0) j.unit_counts[e * S + s] = cnt;
-        if (chain && s != j.trig && nT > 0) {
-            for (int ti = lane; ti < nT; ti += 32)
-                if (t.alive[ti]) {
-                    const float2 m = t.T[ti];
-                    if (!road(j, t, c, m.x, m.y)) t.alive[ti] = 0;
+        if (chain && s != j.trig && ts.n > 0) {
+            for (int ti = lane; ti < ts.n; ti += 32)
+                if (w.alive[ti]) {
+                    const float2 m = w.T[ti];
+                    if (!road<kNBL>(j, t, c, m.x, m.y)) w.alive[ti] = 0;
                 }
             __syncwarp();
         }
@@ -470,17 +660,17 @@ __device__ void light_event_count(const Job& j, WarpTile& t, int lane, const Cut
     int tc = trig_count;
     if (chain) {
         int a = 0;
-        for (int ti = lane; ti < nT; ti += 32) a += t.alive[ti];
+        for (int ti = lane; ti < ts.n; ti += 32) a += w.alive[ti];
         tc = __reduce_add_sync(kFull, a);
     }
     if (lane == 0) {
         j.track_counts[e] = tc;
-        j.ev_class[e] = 0;
+        j.ev_class[e] = kClsLight;
     }
 }
 
-__device__ void light_event_emit(const Job& j, WarpTile& t, int lane, const Cuts& c, int64_t e) {
-    if (j.ev_class[e] != 0) return;
+__device__ void light_event_emit(const Job& j, WarpTile& w, int lane, const Cuts& c, int64_t e) {
+    if (j.ev_class[e] != kClsLight) return;
     const int S = j.S;
     const int nproc = j.mode == 1 ? S : 1;
     bool any = false;
@@ -488,17 +678,19 @@ __device__ void light_event_emit(const Job& j, WarpTile& t, int lane, const Cuts
     if (!any) return;
     EvOff o;
     warp_load_offsets(j, e, lane, o);
+    const TileView<kNBL> t{w.P, w.bst, w.meta};
+    TSink ts{false, nullptr, 0, nullptr, 0};
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
         const int64_t u = e * S + s;
         const int cnt = j.unit_counts[u];
         if (cnt == 0) continue;
-        if (stage_station(j, t, lane, o, s) != 0) {
+        if (stage_station_warp(j, w, lane, o, s) != 0) {
             if (lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
             return;
         }
-        int nT = 0;
-        const int got = enumerate_station<true>(j, t, lane, c, false, nT, j.triplets + 3 * j.trip_off[u], cnt, u);
+        const int got = enum_station<true, kNBL>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
+                                                 nullptr, kClsLight, 0, 1);
         if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
     }
 }
@@ -507,11 +699,11 @@ template <bool EMIT>
 __global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, int persistent) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Job j = *djob;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpTile& t = reinterpret_cast<WarpTile*>(smem_raw)[w];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    WarpTile& w = reinterpret_cast<WarpTile*>(smem_raw)[wi];
     const Cuts c{j.cx, j.cy, j.K};
     if (persistent) {
-        unsigned long long* ctr = &j.ctrl->work[EMIT ? 2 : 0];
+        unsigned long long* ctr = &j.ctrl->work[EMIT ? 3 : 0];
         for (;;) {
             long long e0 = 0;
             if (lane == 0) e0 = (long long)atomicAdd(ctr, (unsigned long long)j.grab);
@@ -520,23 +712,165 @@ __global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, 
             const long long e1 = min(e0 + (long long)j.grab, (long long)j.n_events);
             for (long long e = e0; e < e1; ++e) {
                 if (EMIT)
-                    light_event_emit(j, t, lane, c, e);
+                    light_event_emit(j, w, lane, c, e);
                 else
-                    light_event_count(j, t, lane, c, e);
+                    light_event_count(j, w, lane, c, e);
             }
         }
     } else {
-        const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+        const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + wi;
         if (e < j.n_events) {
             if (EMIT)
-                light_event_emit(j, t, lane, c, e);
+                light_event_emit(j, w, lane, c, e);
             else
-                light_event_count(j, t, lane, c, e);
+                light_event_count(j, w, lane, c, e);
         }
     }
 }
 
-// ----------------------------------------------- block-per-event kernel
+// ------------------------------------------------------ block-tile path
+
+// Stages station s of the event whose offsets are in sm.off.  Returns 0, 1
+// (z <= 0) or 2 (not prunable).
+__device__ int stage_station_block(const Job& j, HeavySmem& sm, int s) {
+    int pbase = 0;
+    for (int l = 0; l < 3; ++l) {
+        const int32_t b = sm.off[3 * s + l], e = sm.off[3 * s + l + 1];
+        int nl = 0;
+        const int st = stage_layer_block(j, sm, l, b, e - b, pbase, nl);
+        if (st) return st;
+        pbase += nl;
+    }
+    return 0;
+}
+
+// One event on the block tile.  In the counting pass the event may move on
+// to the unpruned kernel (too large, extreme coordinates or too many
+// trigger triplets for the block's list).
+template <bool EMIT>
+__device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t e) {
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int S = j.S, S3 = 3 * S;
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    for (int i = tid; i <= S3; i += kHThreads) sm.off[i] = j.off[e * S3 + i];
+    if (tid == 0) sm.s_nT = 0;
+    __syncthreads();
+    if (!EMIT) {
+        bool fits = true;
+        for (int si = 0; si < nproc; ++si) {
+            const int s = station_of(si, j.trig);
+            const int32_t* o = sm.off + 3 * s;
+            if (o[1] - o[0] > kHLayerCap || o[2] - o[1] > kHLayerCap || o[3] - o[2] > kHLayerCap ||
+                o[3] - o[0] > kHHCap)
+                fits = false;
+        }
+        if (!fits) {
+            if (tid == 0) push_event(j, e, kClsGeneric);
+            return;
+        }
+    }
+    const TileView<kNBH> t{sm.P, sm.bst, sm.meta};
+    float2* T = j.tlist + (int64_t)blockIdx.x * j.tlist_cap;
+    uint8_t* alive = j.talive + (int64_t)blockIdx.x * j.tlist_cap;
+    int trig_count = 0, nT = 0;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        const int64_t u = e * S + s;
+        int cnt_expected = 0;
+        if (EMIT) {
+            cnt_expected = j.unit_counts[u];
+            if (cnt_expected == 0) continue;
+        }
+        const int st = stage_station_block(j, sm, s);
+        if (st != 0) {
+            if (tid == 0) {
+                if (EMIT) {
+                    atomicOr(&j.ctrl->status, kStEmitMismatch);
+                } else if (st == 1) {
+                    atomicOr(&j.ctrl->status, kStInvalid);
+                    j.ev_class[e] = kClsInvalid;
+                } else {
+                    push_event(j, e, kClsGeneric);
+                }
+            }
+            return;
+        }
+        if (tid == 0) sm.s_rank = 0;
+        __syncthreads();
+        const bool collect = !EMIT && chain && s == j.trig;
+        TSink ts{collect, T, j.tlist_cap, &sm.s_nT, 0};
+        int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
+        enum_station<EMIT, kNBH>(j, t, sm.queue[wp], lane, c, ts, rows, cnt_expected, u, &sm.s_rank, kClsHeavy, wp,
+                                 kHWarps);
+        __syncthreads();
+        const int cnt = sm.s_rank;
+        if (EMIT) {
+            if (tid == 0 && cnt != cnt_expected) atomicOr(&j.ctrl->status, kStEmitMismatch);
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) j.unit_counts[u] = cnt;
+        if (s == j.trig) trig_count = cnt;
+        if (collect) {
+            nT = sm.s_nT;
+            if (nT > j.tlist_cap) {
+                if (tid == 0) push_event(j, e, kClsGeneric);
+                return;
+            }
+            for (int i = tid; i < nT; i += kHThreads) alive[i] = 1;
+            __syncthreads();
+        }
+        if (chain && s != j.trig && nT > 0) {
+            for (int ti = tid; ti < nT; ti += kHThreads)
+                if (alive[ti]) {
+                    const float2 m = T[ti];
+                    if (!road<kNBH>(j, t, c, m.x, m.y)) alive[ti] = 0;
+                }
+        }
+        __syncthreads();
+    }
+    if (EMIT) return;
+    int tc = trig_count;
+    if (chain) {
+        if (tid == 0) sm.s_cand = 0;
+        __syncthreads();
+        int a = 0;
+        for (int ti = tid; ti < nT; ti += kHThreads) a += alive[ti];
+        a = __reduce_add_sync(kFull, a);
+        if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
+        __syncthreads();
+        tc = sm.s_cand;
+    }
+    if (tid == 0) {
+        if (j.mode == 0)
+            for (int s = 0; s < S; ++s)
+                if (s != j.trig) j.unit_counts[e * S + s] = 0;
+        j.track_counts[e] = tc;
+    }
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(kHThreads, 2) k_heavy(const Job* __restrict__ djob) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
+    const Job j = *djob;
+    const Cuts c{j.cx, j.cy, j.K};
+    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
+    for (;;) {
+        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 4 : 1], 1ull);
+        __syncthreads();
+        const int gi = sm.s_gi;
+        __syncthreads();
+        if (gi >= n_heavy) break;
+        const int64_t e = j.hlist[gi];
+        if (EMIT && j.ev_class[e] != kClsHeavy) continue;
+        heavy_event<EMIT>(j, sm, c, e);
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------- unpruned block path
 
 struct GHit {
     float x, y, z;
@@ -590,7 +924,7 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
     const bool chain = j.mode == 1 && S > 1;
     const int nproc = j.mode == 1 ? S : 1;
     for (;;) {
-        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 3 : 1], 1ull);
+        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 5 : 2], 1ull);
         __syncthreads();
         const int gi = s_gi;
         if (gi >= n_gen) break;
@@ -598,6 +932,7 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
         for (int i = threadIdx.x; i <= S3; i += blockDim.x) soff[i] = j.off[e * S3 + i];
         if (threadIdx.x == 0) s_cand = 0;
         __syncthreads();
+        if (EMIT && j.ev_class[e] != kClsGeneric) continue;
         int trig_count = 0;
         bool bad_event = false;
         for (int si = 0; si < nproc && !bad_event; ++si) {
@@ -615,7 +950,10 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
                     if (__ldg(j.z + h) <= 0.0f) s_bad = 1;
                 __syncthreads();
                 if (s_bad) {
-                    if (threadIdx.x == 0) atomicOr(&j.ctrl->status, kStInvalid);
+                    if (threadIdx.x == 0) {
+                        atomicOr(&j.ctrl->status, kStInvalid);
+                        j.ev_class[e] = kClsInvalid;
+                    }
                     bad_event = true;
                     break;
                 }
@@ -649,12 +987,13 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
                         } else {
                             const unsigned long long b = atomicAdd(&j.ctrl->scratch_n, 1ull);
                             if (b < (unsigned long long)j.tscr_cap) {
-                                TripEntry en;
-                                en.unit = (int32_t)u;
-                                en.rank = rk;
-                                en.ijk = (unsigned long long)i | ((unsigned long long)jx << 21) |
-                                         ((unsigned long long)k << 42) | kFromGeneric;
-                                j.tscr[b] = en;
+                                TripEntry te;
+                                te.unit = (int32_t)u;
+                                te.rank = rk;
+                                te.ijk = (unsigned long long)i | ((unsigned long long)jx << 20) |
+                                         ((unsigned long long)k << 40) |
+                                         ((unsigned long long)kClsGeneric << kTagShift);
+                                j.tscr[b] = te;
                             }
                         }
                     }
@@ -808,28 +1147,29 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Job* __restric
 
 // ------------------------------------------------------ triplet scatter
 
-// Moves each recorded triplet to its row trip_off[unit] + rank.  Entries of
-// events that moved from the warp path to the block path part-way are
-// dropped (the block path recorded the event again).
+// Moves each recorded triplet to its row trip_off[unit] + rank.  Entries
+// written by a path that did not keep the event (it moved on to the next
+// path part-way) are dropped; the final path recorded the event again.
 __global__ void k_scatter(const Job* __restrict__ djob) {
     const Job j = *djob;
     const unsigned long long n = j.ctrl->scratch_n;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        const TripEntry en = j.tscr[q];
-        const int64_t e = en.unit / j.S;
-        const bool from_generic = (en.ijk & kFromGeneric) != 0;
-        if ((j.ev_class[e] == 1) != from_generic) continue;
-        int32_t* r = j.triplets + 3 * (j.trip_off[en.unit] + en.rank);
-        r[0] = (int32_t)(en.ijk & 0x1fffff);
-        r[1] = (int32_t)((en.ijk >> 21) & 0x1fffff);
-        r[2] = (int32_t)((en.ijk >> 42) & 0x1fffff);
+        const TripEntry te = j.tscr[q];
+        const int64_t e = te.unit / j.S;
+        const unsigned tag = (unsigned)((te.ijk >> kTagShift) & 3u);
+        if (j.ev_class[e] != tag) continue;
+        int32_t* r = j.triplets + 3 * (j.trip_off[te.unit] + te.rank);
+        r[0] = (int32_t)(te.ijk & 0xfffffu);
+        r[1] = (int32_t)((te.ijk >> 20) & 0xfffffu);
+        r[2] = (int32_t)((te.ijk >> 40) & 0xfffffu);
     }
 }
 
 // ------------------------------------------------------------ launchers
 
 size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile); }
+size_t heavy_smem_bytes() { return sizeof(HeavySmem); }
 
 static bool g_attr_done = false;
 
@@ -841,6 +1181,10 @@ static cudaError_t ensure_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_light<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)light_smem_bytes(maxw));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
     if (e == cudaSuccess) g_attr_done = true;
     return e;
 }
@@ -849,6 +1193,15 @@ int light_max_blocks_per_sm(int wpb) {
     if (ensure_attrs() != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_light<false>, wpb * 32, light_smem_bytes(wpb)) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int heavy_max_blocks_per_sm() {
+    if (ensure_attrs() != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heavy<false>, kHThreads, heavy_smem_bytes()) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -878,6 +1231,7 @@ cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCf
 }
 
 cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
     k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
     k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
     k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
@@ -903,6 +1257,7 @@ cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg
         const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
         k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
     }
+    k_heavy<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
     k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
     return cudaGetLastError();
 }

@@ -223,3 +223,45 @@ def test_autotune_keeps_results(lib, synth_mod):
     assert s == 0
     after = gpu_select(ctx, b)
     assert_same(after, before, 16000)
+
+
+def test_dense_trigger_moves_to_block_tile(lib, oracle_mod):
+    # 9 hits per layer on nearly one line: 9^3 passing trigger triplets, more
+    # than a warp keeps, so the event runs on the block tile
+    rng = np.random.default_rng(31)
+    events = []
+    for _ in range(20):
+        tx, ty = rng.uniform(-0.3, 0.3, 2)
+        zl = [120.0, 130.0, 140.0, 155.0, 165.0, 175.0]
+        ev = []
+        for z in zl:
+            ev.append([(tx * z + rng.normal(0, 0.05), ty * z + rng.normal(0, 0.05), z) for _ in range(9)])
+        events.append(ev)
+    b = make_batch(events, 2)
+    for mode in (0, 1):
+        ref = _oracle(oracle_mod, 2, mode, 0.25, 0.25, b)
+        assert ref["track_counts"].max() > 64
+        ctx = _ctx(lib, 2, mode)
+        for form in ("plain", "batched"):
+            assert_same(gpu_select(ctx, b, form=form), ref, 40, label=f"mode={mode} {form}")
+
+
+def test_huge_layer_goes_unpruned(lib, oracle_mod):
+    # a layer above the block tile's 2048 hits: the unpruned kernel takes it
+    rng = np.random.default_rng(32)
+    events = []
+    for n in (2100, 50, 2300):
+        z = [120.0, 130.0, 140.0]
+        ev = []
+        for li in range(3):
+            m = n if li == 1 else 40
+            r = rng.uniform(15, 0.4 * z[li], m)
+            ph = rng.uniform(0, 2 * np.pi, m)
+            hits = [(float(a * np.cos(p)), float(a * np.sin(p)), z[li]) for a, p in zip(r, ph)]
+            hits.append((0.1 * z[li], -0.05 * z[li], z[li]))
+            ev.append(hits)
+        events.append(ev)
+    b = make_batch(events, 1)
+    ref = _oracle(oracle_mod, 1, 1, 0.25, 0.25, b)
+    assert ref["trip_needed"] >= 3
+    assert_same(gpu_select(_ctx(lib, 1, 1), b), ref, 3)
