@@ -169,6 +169,199 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def percentiles(v, qs=(50, 99, 99.9)):
+    a = np.sort(np.asarray(v, dtype=np.float64))
+    return {f"p{q:g}": float(a[min(len(a) - 1, int(np.ceil(q / 100 * len(a))) - 1)]) for q in qs}
+
+
+def run_timeslices(args, w, dev, jp, torch):
+    """Uneven timeslices (log-normal multiplicities): one jpsi_run per
+    timeslice (persistent kernels replayed from the captured graph) against
+    one jpsi_run_plain per timeslice, all data resident."""
+    import synth
+    sizes = synth.timeslice_sizes(w, args.slices)
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    p = jp.params(**params_kw(args, w))
+    ctx = jp.Context(p, device=dev.index, hbm_budget=64 << 30)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    slices = []
+    t0 = time.perf_counter()
+    n_hits_tot = 0
+    for e0, n in zip(starts, sizes):
+        b = synth.generate(w, int(e0), int(n))
+        d = {k: torch.from_numpy(b[k]).to(dev) for k in ("x", "y", "z", "offsets")}
+        batch = jp.make_batch(d["x"], d["y"], d["z"], d["offsets"], int(n), b["n_hits"])
+        nu = int(n) * w.n_stations
+        o = jp.jpsi_outputs()
+        acc = torch.empty((int(n) + 31) // 32, dtype=torch.int32, device=dev)
+        tc = torch.empty(int(n), dtype=torch.int32, device=dev)
+        toff = torch.empty(nu + 1, dtype=torch.int64, device=dev)
+        o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
+        ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))
+        trip = torch.empty((max(o.trip_needed, 1), 3), dtype=torch.int32, device=dev)
+        o.triplets, o.trip_capacity = trip.data_ptr(), o.trip_needed
+        slices.append((d, batch, o, acc, tc, toff, trip))
+        n_hits_tot += b["n_hits"]
+    gen_s = time.perf_counter() - t0
+    # the autotuner picks the batched form's launch shape on one timeslice
+    mid = slices[len(slices) // 2]
+    if not args.no_autotune:
+        ctx.check(jp.jpsi_autotune(ctx.ctx, mid[1]))
+    stream = torch.cuda.current_stream(dev)
+
+    def sweep(fn):
+        for s_ in slices:  # warm-up (graph capture, scratch growth)
+            ctx.check(fn(ctx.ctx, s_[1], s_[2], st))
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(slices) + 1)]
+        jp.jpsi_timing_enable(ctx.ctx, True)
+        ev[0].record(stream)
+        for i, s_ in enumerate(slices):
+            ctx.check(fn(ctx.ctx, s_[1], s_[2], st))
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        tm = jp.jpsi_timing_get(ctx.ctx)
+        jp.jpsi_timing_enable(ctx.ctx, False)
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(slices))]
+        return sum(per), per, tm
+
+    clocks = Clocks(dev.index)
+    clocks.start()
+    tb, per_b, tm_b = sweep(jp.jpsi_run)
+    clk = clocks.stop()
+    tp, per_p, _ = sweep(jp.jpsi_run_plain)
+    n_ev = int(sizes.sum())
+    line = {"metric": METRIC, "value": n_ev / (tb / 1000), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "timeslices": len(sizes), "events": n_ev, "hits": n_hits_tot,
+                       "slice_events_min": int(sizes.min()), "slice_events_max": int(sizes.max()),
+                       "mode": args.mode, "window_cm": w.window},
+            "plain": {"value": n_ev / (tp / 1000), "ms_total": tp},
+            "speedup_batched_vs_plain": tp / tb,
+            "slice_latency_ms": {"batched": percentiles(per_b, (50, 99)), "plain": percentiles(per_p, (50, 99))},
+            "phases_ms": {"light_count": tm_b.light_ms, "count_rest": tm_b.count_rest_ms, "emit": tm_b.emit_ms},
+            "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serving(args, w, dev, jp, torch):
+    """Continuous batching: timeslices of U[2e3, 2e5] events arrive as a
+    Poisson process; jpsi_serve_submit admits each into a resident device slot
+    as soon as one frees up (a blocking submit is the back-pressure) and runs
+    it on that slot's stream while other slots copy or compute.  Latency =
+    completion (outputs in host memory) - arrival.  Offered loads: the
+    workload's 10^7 events/s, saturation (all requests at t=0), and 50/80/95 %
+    of the saturated throughput."""
+    import threading
+
+    import synth
+    n_req = args.slices or 64
+    pool_n = min(args.pool, n_req)
+    sizes_all = synth.timeslice_sizes(w, n_req)
+    p = jp.params(**params_kw(args, w))
+    ctx = jp.Context(p, device=dev.index, hbm_budget=args.serve_budget_gb << 30)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    pool, e0 = [], 0
+    t0 = time.perf_counter()
+    for i in range(pool_n):
+        n = int(sizes_all[i])
+        b = synth.generate(w, e0, n)
+        e0 += n
+        h = {k: torch.from_numpy(b[k]).pin_memory() for k in ("x", "y", "z", "offsets")}
+        # exact triplet count of this timeslice, to size the slots
+        d = {k: v.to(dev) for k, v in h.items()}
+        o = jp.jpsi_outputs()
+        ctx.check(jp.jpsi_run(ctx.ctx, jp.make_batch(d["x"], d["y"], d["z"], d["offsets"], n, b["n_hits"]), o, st))
+        pool.append({"h": h, "n": n, "hits": b["n_hits"], "trip": o.trip_needed})
+        del d
+    gen_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    S = w.n_stations
+    slot_events = max(q["n"] for q in pool)
+    slot_hits = max(q["hits"] for q in pool)
+    slot_trip = max(q["trip"] for q in pool)
+    ctx.check(jp.jpsi_serve_start(ctx.ctx, args.slots, slot_events, slot_hits, slot_trip))
+    reqs = [pool[i % pool_n] for i in range(n_req)]
+    outs = []
+    for q in reqs:
+        n = q["n"]
+        ob = {"acc": torch.empty((n + 31) // 32, dtype=torch.int32, pin_memory=True),
+              "tc": torch.empty(n, dtype=torch.int32, pin_memory=True),
+              "toff": torch.empty(n * S + 1, dtype=torch.int64, pin_memory=True),
+              "trip": torch.empty((max(q["trip"], 1), 3), dtype=torch.int32, pin_memory=True)}
+        o = jp.jpsi_outputs()
+        o.accept_bits, o.track_counts = ob["acc"].data_ptr(), ob["tc"].data_ptr()
+        o.trip_off, o.triplets, o.trip_capacity = ob["toff"].data_ptr(), ob["trip"].data_ptr(), q["trip"]
+        hb = jp.make_batch(q["h"]["x"], q["h"]["y"], q["h"]["z"], q["h"]["offsets"], n, q["hits"])
+        outs.append((hb, o, ob))
+    n_events = sum(q["n"] for q in reqs)
+
+    def run_load(rate):
+        mean = n_events / n_req
+        if rate is None:
+            arr = np.zeros(n_req)
+        else:
+            rng = np.random.Generator(np.random.PCG64(w.seed * 7919 + int(rate)))
+            arr = np.cumsum(rng.exponential(mean / rate, size=n_req))
+            arr -= arr[0]
+        subs = [None] * n_req
+        t_start = time.perf_counter() + 0.05
+
+        def submitter():
+            for i in range(n_req):
+                delay = t_start + arr[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tc0 = time.perf_counter()
+                s_, tk = jp.jpsi_serve_submit(ctx.ctx, outs[i][0], outs[i][1])
+                subs[i] = (s_, tk, tc0 - (t_start + arr[i]))
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, done = [], []
+        for i in range(n_req):
+            while subs[i] is None:
+                time.sleep(0.0002)
+            s_, tk, queued = subs[i]
+            assert s_ == 0, s_
+            ws, rs, lat_lib = jp.jpsi_serve_wait(ctx.ctx, tk, 60000)
+            assert ws == 0 and rs == 0, (ws, rs)
+            lat.append(queued + lat_lib)
+            done.append(arr[i] + queued + lat_lib)
+        th.join()
+        span = max(done)
+        return {"offered_events_per_s": None if rate is None else rate, "sustained_events_per_s": n_events / span,
+                "latency_ms": {k: 1000 * v for k, v in percentiles(lat).items()}}
+
+    run_load(None)  # warm-up: graphs, buffers
+    sat = run_load(None)
+    cap = sat["sustained_events_per_s"]
+    loads = [run_load(w.extra["rate_events_per_s"])]
+    for f in (0.5, 0.8, 0.95):
+        r = run_load(f * cap)
+        r["fraction_of_saturation"] = f
+        loads.append(r)
+    # isolation: a served result equals the same timeslice run alone
+    hb, o, ob = outs[0]
+    solo = {"acc": torch.empty_like(ob["acc"]), "tc": torch.empty_like(ob["tc"]), "toff": torch.empty_like(ob["toff"]),
+            "trip": torch.empty_like(ob["trip"])}
+    o2 = jp.jpsi_outputs()
+    o2.accept_bits, o2.track_counts = solo["acc"].data_ptr(), solo["tc"].data_ptr()
+    o2.trip_off, o2.triplets, o2.trip_capacity = solo["toff"].data_ptr(), solo["trip"].data_ptr(), o.trip_capacity
+    ctx.check(jp.jpsi_serve_stop(ctx.ctx))
+    ctx.check(jp.jpsi_run_host(ctx.ctx, hb, o2, st))
+    same = all(torch.equal(solo[k], ob[k]) for k in ("acc", "tc", "toff"))
+    line = {"metric": METRIC, "value": cap, "unit": UNIT, "n_gpus": 1, "steps": len(loads) + 2, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "requests": n_req, "distinct_timeslices": pool_n, "events": n_events,
+                       "slots": args.slots, "slot_events": slot_events, "slot_hits": slot_hits,
+                       "hbm_budget_gb": args.serve_budget_gb, "mode": args.mode},
+            "saturation": sat, "loads": loads, "isolation_counts_equal": bool(same), "generate_s": gen_s}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def params_kw(args, w):
     t = w.window ** 2
     return {"n_stations": w.n_stations, "mode": 1 if args.mode == "chain" else 0, "t_xz": t, "t_yz": t}
@@ -188,6 +381,11 @@ def main():
     ap.add_argument("--ref-events", type=int, default=40_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="(for ncu) run this many steps and exit")
+    ap.add_argument("--slices", type=int, default=None, help="timeslices (timeslice/stream workloads)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--pool", type=int, default=8, help="distinct timeslices generated for the stream workload")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=int, default=16)
     args = ap.parse_args()
     rank, world, local = dist_info()
     if args.warmup < 3 and not args.profile_steps:
@@ -209,6 +407,10 @@ def main():
         pg = dist
     jp.load(build_if_missing=True)
     w = synth.WORKLOADS[args.workload]
+    if w.name == "lognormal_timeslices":
+        return run_timeslices(args, w, dev, jp, torch)
+    if w.name == "lognormal_stream":
+        return run_serving(args, w, dev, jp, torch)
     n_ev = args.events or w.n_events
     S = w.n_stations
 

@@ -43,7 +43,7 @@ struct RunState {
     Job* h_job = nullptr;     // pinned
     Ctrl* d_ctrl = nullptr;
     Ctrl* h_ctrl = nullptr;   // pinned
-    DevBuf unit_counts, track_counts, ev_class, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
+    DevBuf unit_counts, track_counts, ev_class, mlist, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
     cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr, g_scatter = nullptr;
     int g_cfg_id = -1;
@@ -211,6 +211,7 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     jpsi_status st;
     if ((st = ensure(c, rs.unit_counts, (size_t)std::max<int64_t>(nu, 1) * 4, "unit counts")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.ev_class, (size_t)std::max<int64_t>(ne, 1), "event classes")) != JPSI_OK) return st;
+    if ((st = ensure(c, rs.mlist, (size_t)std::max<int64_t>(ne, 1) * 4, "event list")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.hlist, (size_t)std::max<int64_t>(ne, 1) * 4, "event list")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.glist, (size_t)std::max<int64_t>(ne, 1) * 4, "event list")) != JPSI_OK) return st;
     const size_t tl = (size_t)std::max(c->batch_cfg.heavy_blocks, c->plain_cfg.heavy_blocks) * kHeavyTCap;
@@ -239,6 +240,7 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.unit_counts = (int32_t*)rs.unit_counts.p;
     j.track_counts = o->track_counts ? o->track_counts : (int32_t*)rs.track_counts.p;
     j.ev_class = (uint8_t*)rs.ev_class.p;
+    j.mlist = (int32_t*)rs.mlist.p;
     j.hlist = (int32_t*)rs.hlist.p;
     j.glist = (int32_t*)rs.glist.p;
     j.tlist = (float2*)rs.tlist.p;
@@ -302,6 +304,7 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.unit_counts);
     release(c, rs.track_counts);
     release(c, rs.ev_class);
+    release(c, rs.mlist);
     release(c, rs.hlist);
     release(c, rs.glist);
     release(c, rs.tlist);
@@ -421,11 +424,13 @@ void set_launch_shape(jpsi_ctx* c, int wpb, int grab) {
     const int lb = std::max(1, light_max_blocks_per_sm(wpb));
     const int gb = std::max(1, generic_max_blocks_per_sm(256));
     const int hb = std::max(1, heavy_max_blocks_per_sm());
+    const int mb = std::max(1, medium_max_blocks_per_sm());
     c->batch_cfg.light_wpb = wpb;
     c->batch_cfg.light_blocks = c->n_sm * lb;
     c->batch_cfg.generic_threads = 256;
     c->batch_cfg.generic_blocks = c->n_sm * gb;
     c->batch_cfg.heavy_blocks = c->n_sm * hb;
+    c->batch_cfg.medium_blocks = c->n_sm * mb;
     c->batch_cfg.scan_blocks = c->n_sm * 2;
     c->plain_cfg = c->batch_cfg;
     c->plain_cfg.light_wpb = 4;
@@ -732,6 +737,7 @@ jpsi_status jpsi_serve_start(jpsi_ctx* c, int n_slots, int64_t slot_events, int6
             (s = ensure(c, sl->rs.ev_class, (size_t)ne, "slot classes")) ||
             (s = ensure(c, sl->rs.track_counts, (size_t)ne * 4, "slot track scratch")) ||
             (s = ensure(c, sl->rs.trip_off, (size_t)(nu + 1) * 8, "slot offsets scratch")) ||
+            (s = ensure(c, sl->rs.mlist, (size_t)ne * 4, "slot list")) ||
             (s = ensure(c, sl->rs.hlist, (size_t)ne * 4, "slot list")) ||
             (s = ensure(c, sl->rs.glist, (size_t)ne * 4, "slot list")) ||
             (s = ensure(c, sl->rs.tlist, (size_t)c->batch_cfg.heavy_blocks * kHeavyTCap * sizeof(float2), "slot trigger lists")) ||

@@ -17,9 +17,8 @@ enum : int32_t {
 };
 
 // A passing triplet recorded by the counting pass: unit, rank inside the
-// unit, (i, j, k) packed 20 bits each, and in bits 60-61 the path that wrote
-// it (0 warp, 1 block tile, 2 unpruned block), which must match the path that
-// finally owned the event.
+// unit, (i, j, k) packed 20 bits each, and in bits 60-62 the class of the
+// path that wrote it, which must match the path that finally owned the event.
 struct TripEntry {
     int32_t unit;
     int32_t rank;
@@ -29,15 +28,15 @@ constexpr int kTagShift = 60;
 constexpr int32_t kPackLimit = 1 << 20;
 
 // Event classes (Job::ev_class).
-enum : uint8_t { kClsLight = 0, kClsHeavy = 1, kClsInvalid = 2, kClsGeneric = 3 };
+enum : uint8_t { kClsLight = 0, kClsHeavy = 1, kClsInvalid = 2, kClsGeneric = 3, kClsMedium = 4 };
 
 // Device-resident control block of one run (zeroed before each run).
 struct Ctrl {
     int32_t status;
+    int32_t n_medium;             // events sent to the medium warp kernel
     int32_t n_heavy;              // events sent to the block-tile kernel
     int32_t n_generic;            // events sent to the unpruned block kernel
-    int32_t pad0;
-    unsigned long long work[6];   // persistent work counters: light, heavy, generic (count); same (emit)
+    unsigned long long work[8];   // persistent work counters: small, medium, heavy, generic (count); same (emit)
     int64_t trip_total;           // copy of trip_off[n_units]
     unsigned long long scratch_n; // triplet entries appended by the counting pass
 };
@@ -57,6 +56,7 @@ struct Job {
     int32_t* unit_counts;         // [n_events*S]
     int32_t* track_counts;        // [n_events]
     uint8_t* ev_class;            // [n_events]: kCls*
+    int32_t* mlist;               // [n_events] events for the medium warp kernel
     int32_t* hlist;               // [n_events] events for the block-tile kernel
     int32_t* glist;               // [n_events] events for the unpruned block kernel
     float2* tlist;                // [heavy blocks * tlist_cap] trigger slopes (block-tile kernel)
@@ -74,6 +74,7 @@ struct Job {
 struct LaunchCfg {
     int light_wpb = 4;            // warps per block of the warp-per-event kernel
     int light_blocks = 0;         // persistent grid (0 = static, one warp per event)
+    int medium_blocks = 0;        // grid of the medium warp kernel (4 warps per block)
     int generic_threads = 256;
     int generic_blocks = 0;       // grid of the unpruned block kernel
     int heavy_blocks = 0;         // grid of the block-tile kernel
@@ -81,12 +82,13 @@ struct LaunchCfg {
 };
 
 // Launchers (jpsi_kernels.cu).  All asynchronous on `st`.
-// Count phase = light kernel, then the rest (block-tile kernel, unpruned
-// block kernel, accept bits, scan).  Kernel launches per call: 1 and 6.
+// Count phase = small warp kernel, then the rest (medium warp kernel,
+// block-tile kernel, unpruned block kernel, accept bits, scan).  Kernel
+// launches per call: 1 and 7.
 cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st);
 cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
-constexpr int kLaunchesLight = 1, kLaunchesRest = 6, kLaunchesEmit = 3;
+constexpr int kLaunchesLight = 1, kLaunchesRest = 7, kLaunchesEmit = 4;
 // Places the counting pass's triplet entries at trip_off[unit] + rank.
 cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesScatter = 1;
@@ -98,6 +100,7 @@ size_t light_smem_bytes(int wpb);
 int light_max_blocks_per_sm(int wpb);
 int generic_max_blocks_per_sm(int threads);
 int heavy_max_blocks_per_sm();
+int medium_max_blocks_per_sm();
 size_t heavy_smem_bytes();
 constexpr int kHeavyTCap = 1 << 15;  // trigger triplets per event on the block-tile path
 const void* light_count_kernel_ptr();

@@ -42,12 +42,19 @@ namespace jpsi {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQCap = 128;                // pair queue entries per warp
 
-// warp path
-constexpr int kRMax = 6;                  // hits per lane per layer
-constexpr int kLayerCap = 32 * kRMax;     // 192 hits per layer
-constexpr int kHCap = 384;                // hits per station tile
+// warp path: tile shape per variant
 constexpr int kTCap = 64;                 // passing trigger triplets per event (CHAIN)
-constexpr int kNBL = 64;                  // slope bins per layer
+template <int RMAX_, int HCAP_, int NB_, uint8_t CLS_, int WPB_>
+struct WCfg {
+    static constexpr int RMAX = RMAX_;              // hits per lane per layer
+    static constexpr int LAYER_CAP = 32 * RMAX_;    // hits per layer
+    static constexpr int HCAP = HCAP_;              // hits per station tile
+    static constexpr int NB = NB_;                  // slope bins per layer
+    static constexpr uint8_t CLS = CLS_;            // event class of this path
+    static constexpr int WPB = WPB_;                // warps per block (medium: fixed)
+};
+using SmallCfg = WCfg<6, 384, 64, kClsLight, 0>;      // 192 hits/layer, 384/station
+using MediumCfg = WCfg<12, 960, 128, kClsMedium, 4>;  // 384 hits/layer, 960/station
 
 // block-tile path
 constexpr int kHThreads = 256;
@@ -74,14 +81,15 @@ struct TileView {
     __device__ __forceinline__ int bin_start(int l, int b) const { return bst[l * (NB + 1) + b]; }
 };
 
+template <class Cfg>
 struct WarpTile {
-    float4 P[kHCap];
+    float4 P[Cfg::HCAP];
     uint32_t queue[kQCap];
     float2 T[kTCap];            // trigger triplet slopes
     uint8_t alive[kTCap];
-    uint16_t bst[3 * (kNBL + 1)];
+    uint16_t bst[3 * (Cfg::NB + 1)];
     LayerMeta meta[3];
-    uint32_t hist[kNBL];        // bin counts of the layer being staged
+    uint32_t hist[Cfg::NB];     // bin counts of the layer being staged
 };
 
 struct HeavySmem {
@@ -173,21 +181,23 @@ __device__ bool warp_load_offsets(const Job& j, int64_t e, int lane, EvOff& o) {
 // hit whose pruning bound is not finite).  Hits are counted into slope bins
 // with shared-memory atomics (the order inside a bin is not fixed; results
 // do not depend on it) and written sorted by bin.
-__device__ int stage_layer_warp(const Job& j, WarpTile& w, int l, int32_t base, int32_t n, int32_t pbase, int lane,
-                                int& nlive) {
-    float sx[kRMax], sy[kRMax], bb[kRMax];
-    bool lv[kRMax];
+template <class Cfg>
+__device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t base, int32_t n, int32_t pbase,
+                                int lane, int& nlive) {
+    constexpr int R = Cfg::RMAX, NB = Cfg::NB, BPL = NB / 32;  // bins per lane
+    float sx[R], sy[R], bb[R];
+    bool lv[R];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
-    w.hist[2 * lane] = 0;
-    w.hist[2 * lane + 1] = 0;
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r) {
+    for (int q = 0; q < BPL; ++q) w.hist[BPL * lane + q] = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
         lv[r] = false;
         sx[r] = sy[r] = bb[r] = 0.0f;
     }
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r) {
+    for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;  // warp-uniform
         const int h = lane + 32 * r;
         const bool in = h < n;
@@ -210,37 +220,46 @@ __device__ int stage_layer_warp(const Job& j, WarpTile& w, int l, int32_t base, 
     bmax = warp_max(bmax);
     float inv_w = 0.0f;
     if (hi > lo) {
-        inv_w = __fdiv_rn((float)kNBL, __fsub_rn(hi, lo));
+        inv_w = __fdiv_rn((float)NB, __fsub_rn(hi, lo));
         if (!(inv_w < INFINITY)) inv_w = 0.0f;
     }
     __syncwarp();
-    int bin[kRMax], rank[kRMax];
+    int bin[R], rank[R];
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r) {
+    for (int r = 0; r < R; ++r) {
         bin[r] = 0;
         rank[r] = 0;
     }
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r) {
+    for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
         if (lv[r]) {
-            bin[r] = slope_bin<kNBL>(sx[r], lo, inv_w);
+            bin[r] = slope_bin<NB>(sx[r], lo, inv_w);
             rank[r] = (int)atomicAdd(&w.hist[bin[r]], 1u);
         }
     }
     __syncwarp();
-    // exclusive scan of the 64 bin counts, two per lane
-    const int c0 = (int)w.hist[2 * lane], c1 = (int)w.hist[2 * lane + 1];
-    const int cnt = c0 + c1;
+    // exclusive scan of the NB bin counts, NB/32 consecutive bins per lane
+    int cs[BPL];
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+        cs[q] = (int)w.hist[BPL * lane + q];
+        cnt += cs[q];
+    }
     const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    uint16_t* bst = w.bst + l * (kNBL + 1);
-    bst[2 * lane] = (uint16_t)(pbase + incl - cnt);
-    bst[2 * lane + 1] = (uint16_t)(pbase + incl - cnt + c0);
-    if (lane == 31) bst[kNBL] = (uint16_t)(pbase + total);
+    uint16_t* bst = w.bst + l * (NB + 1);
+    int run = pbase + incl - cnt;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+        bst[BPL * lane + q] = (uint16_t)run;
+        run += cs[q];
+    }
+    if (lane == 31) bst[NB] = (uint16_t)(pbase + total);
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < kRMax; ++r) {
+    for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
         if (lv[r]) w.P[bst[bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(lane + 32 * r));
     }
@@ -259,12 +278,13 @@ __device__ int stage_layer_warp(const Job& j, WarpTile& w, int l, int32_t base, 
     return 0;
 }
 
-__device__ int stage_station_warp(const Job& j, WarpTile& w, int lane, const EvOff& o, int s) {
+template <class Cfg>
+__device__ int stage_station_warp(const Job& j, WarpTile<Cfg>& w, int lane, const EvOff& o, int s) {
     int pbase = 0;
     for (int l = 0; l < 3; ++l) {
         const int32_t b = off_get(o, s * 3 + l), e = off_get(o, s * 3 + l + 1);
         int nl = 0;
-        const int st = stage_layer_warp(j, w, l, b, e - b, pbase, lane, nl);
+        const int st = stage_layer_warp<Cfg>(j, w, l, b, e - b, pbase, lane, nl);
         if (st) return st;
         pbase += nl;
     }
@@ -584,7 +604,10 @@ __device__ bool road(const Job& j, const TileView<NB>& t, const Cuts& c, float m
 
 __device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls) {
     j.ev_class[e] = cls;
-    if (cls == kClsHeavy) {
+    if (cls == kClsMedium) {
+        const int gi = atomicAdd(&j.ctrl->n_medium, 1);
+        j.mlist[gi] = (int32_t)e;
+    } else if (cls == kClsHeavy) {
         const int gi = atomicAdd(&j.ctrl->n_heavy, 1);
         j.hlist[gi] = (int32_t)e;
     } else {
@@ -593,10 +616,28 @@ __device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls)
     }
 }
 
-__device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cuts& c, int64_t e) {
+// Does an event fit a warp tile of this shape (processed stations only)?
+template <class Cfg>
+__device__ __forceinline__ bool fits_warp(const Job& j, const EvOff& o, int nproc) {
+    bool fits = true;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        const int32_t o0 = off_get(o, 3 * s), o1 = off_get(o, 3 * s + 1), o2 = off_get(o, 3 * s + 2),
+                      o3 = off_get(o, 3 * s + 3);
+        if (o1 - o0 > Cfg::LAYER_CAP || o2 - o1 > Cfg::LAYER_CAP || o3 - o2 > Cfg::LAYER_CAP || o3 - o0 > Cfg::HCAP)
+            fits = false;
+    }
+    return fits;
+}
+
+template <class Cfg>
+__device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, const Cuts& c, int64_t e) {
+    constexpr int NB = Cfg::NB;
+    constexpr bool kSmall = Cfg::CLS == kClsLight;
     EvOff o;
     const int S = j.S;
-    if (!warp_load_offsets(j, e, lane, o)) {
+    const bool valid = warp_load_offsets(j, e, lane, o);
+    if (kSmall && !valid) {
         if (lane == 0) {
             atomicOr(&j.ctrl->status, kStInvalid);
             j.ev_class[e] = kClsInvalid;
@@ -605,23 +646,18 @@ __device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cut
     }
     const bool chain = j.mode == 1 && S > 1;
     const int nproc = j.mode == 1 ? S : 1;
-    bool fits = true;
-    for (int si = 0; si < nproc; ++si) {
-        const int s = station_of(si, j.trig);
-        const int32_t o0 = off_get(o, 3 * s), o1 = off_get(o, 3 * s + 1), o2 = off_get(o, 3 * s + 2),
-                      o3 = off_get(o, 3 * s + 3);
-        if (o1 - o0 > kLayerCap || o2 - o1 > kLayerCap || o3 - o2 > kLayerCap || o3 - o0 > kHCap) fits = false;
-    }
-    if (!fits) {
-        if (lane == 0) push_event(j, e, kClsHeavy);
+    if (!fits_warp<Cfg>(j, o, nproc)) {
+        // all lanes take part in the shuffles of the size check
+        const bool to_medium = kSmall && fits_warp<MediumCfg>(j, o, nproc);
+        if (lane == 0) push_event(j, e, to_medium ? kClsMedium : kClsHeavy);
         return;
     }
-    const TileView<kNBL> t{w.P, w.bst, w.meta};
+    const TileView<NB> t{w.P, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
-        const int st = stage_station_warp(j, w, lane, o, s);
+        const int st = stage_station_warp<Cfg>(j, w, lane, o, s);
         if (st == 1) {
             if (lane == 0) {
                 atomicOr(&j.ctrl->status, kStInvalid);
@@ -634,8 +670,8 @@ __device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cut
             return;
         }
         ts.on = chain && s == j.trig;
-        const int cnt = enum_station<false, kNBL>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr,
-                                                  kClsLight, 0, 1);
+        const int cnt = enum_station<false, NB>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
+                                                0, 1);
         if (ts.on) {
             if (ts.n > kTCap) {
                 if (lane == 0) push_event(j, e, kClsHeavy);
@@ -651,7 +687,7 @@ __device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cut
             for (int ti = lane; ti < ts.n; ti += 32)
                 if (w.alive[ti]) {
                     const float2 m = w.T[ti];
-                    if (!road<kNBL>(j, t, c, m.x, m.y)) w.alive[ti] = 0;
+                    if (!road<NB>(j, t, c, m.x, m.y)) w.alive[ti] = 0;
                 }
             __syncwarp();
         }
@@ -665,12 +701,14 @@ __device__ void light_event_count(const Job& j, WarpTile& w, int lane, const Cut
     }
     if (lane == 0) {
         j.track_counts[e] = tc;
-        j.ev_class[e] = kClsLight;
+        j.ev_class[e] = Cfg::CLS;
     }
 }
 
-__device__ void light_event_emit(const Job& j, WarpTile& w, int lane, const Cuts& c, int64_t e) {
-    if (j.ev_class[e] != kClsLight) return;
+template <class Cfg>
+__device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const Cuts& c, int64_t e) {
+    constexpr int NB = Cfg::NB;
+    if (j.ev_class[e] != Cfg::CLS) return;
     const int S = j.S;
     const int nproc = j.mode == 1 ? S : 1;
     bool any = false;
@@ -678,53 +716,73 @@ __device__ void light_event_emit(const Job& j, WarpTile& w, int lane, const Cuts
     if (!any) return;
     EvOff o;
     warp_load_offsets(j, e, lane, o);
-    const TileView<kNBL> t{w.P, w.bst, w.meta};
+    const TileView<NB> t{w.P, w.bst, w.meta};
     TSink ts{false, nullptr, 0, nullptr, 0};
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
         const int64_t u = e * S + s;
         const int cnt = j.unit_counts[u];
         if (cnt == 0) continue;
-        if (stage_station_warp(j, w, lane, o, s) != 0) {
+        if (stage_station_warp<Cfg>(j, w, lane, o, s) != 0) {
             if (lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
             return;
         }
-        const int got = enum_station<true, kNBL>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
-                                                 nullptr, kClsLight, 0, 1);
+        const int got = enum_station<true, NB>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
+                                               nullptr, Cfg::CLS, 0, 1);
         if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
     }
 }
 
+template <bool EMIT, class Cfg>
+__device__ __forceinline__ void light_event(const Job& j, WarpTile<Cfg>& w, int lane, const Cuts& c, int64_t e) {
+    if (EMIT)
+        light_event_emit<Cfg>(j, w, lane, c, e);
+    else
+        light_event_count<Cfg>(j, w, lane, c, e);
+}
+
+// Small warp tiles: every event of the batch (statically one warp per event,
+// or persistent warps grabbing `grab` events at a time).
 template <bool EMIT>
 __global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, int persistent) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Job j = *djob;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    WarpTile& w = reinterpret_cast<WarpTile*>(smem_raw)[wi];
+    WarpTile<SmallCfg>& w = reinterpret_cast<WarpTile<SmallCfg>*>(smem_raw)[wi];
     const Cuts c{j.cx, j.cy, j.K};
     if (persistent) {
-        unsigned long long* ctr = &j.ctrl->work[EMIT ? 3 : 0];
+        unsigned long long* ctr = &j.ctrl->work[EMIT ? 4 : 0];
         for (;;) {
             long long e0 = 0;
             if (lane == 0) e0 = (long long)atomicAdd(ctr, (unsigned long long)j.grab);
             e0 = __shfl_sync(kFull, e0, 0);
             if (e0 >= j.n_events) break;
             const long long e1 = min(e0 + (long long)j.grab, (long long)j.n_events);
-            for (long long e = e0; e < e1; ++e) {
-                if (EMIT)
-                    light_event_emit(j, w, lane, c, e);
-                else
-                    light_event_count(j, w, lane, c, e);
-            }
+            for (long long e = e0; e < e1; ++e) light_event<EMIT, SmallCfg>(j, w, lane, c, e);
         }
     } else {
         const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + wi;
-        if (e < j.n_events) {
-            if (EMIT)
-                light_event_emit(j, w, lane, c, e);
-            else
-                light_event_count(j, w, lane, c, e);
-        }
+        if (e < j.n_events) light_event<EMIT, SmallCfg>(j, w, lane, c, e);
+    }
+}
+
+// Medium warp tiles: the events the small tiles passed on, one at a time per
+// warp from the medium list.
+template <bool EMIT>
+__global__ void __launch_bounds__(128, 3) k_medium(const Job* __restrict__ djob) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Job j = *djob;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    WarpTile<MediumCfg>& w = reinterpret_cast<WarpTile<MediumCfg>*>(smem_raw)[wi];
+    const Cuts c{j.cx, j.cy, j.K};
+    const int n_med = *(volatile int32_t*)&j.ctrl->n_medium;
+    unsigned long long* ctr = &j.ctrl->work[EMIT ? 5 : 1];
+    for (;;) {
+        int gi = 0;
+        if (lane == 0) gi = (int)atomicAdd(ctr, 1ull);
+        gi = __shfl_sync(kFull, gi, 0);
+        if (gi >= n_med) break;
+        light_event<EMIT, MediumCfg>(j, w, lane, c, j.mlist[gi]);
     }
 }
 
@@ -858,7 +916,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_heavy(const Job* __restrict__ 
     const Cuts c{j.cx, j.cy, j.K};
     const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
     for (;;) {
-        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 4 : 1], 1ull);
+        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 6 : 2], 1ull);
         __syncthreads();
         const int gi = sm.s_gi;
         __syncthreads();
@@ -924,7 +982,7 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
     const bool chain = j.mode == 1 && S > 1;
     const int nproc = j.mode == 1 ? S : 1;
     for (;;) {
-        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 5 : 2], 1ull);
+        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 7 : 3], 1ull);
         __syncthreads();
         const int gi = s_gi;
         if (gi >= n_gen) break;
@@ -1157,7 +1215,7 @@ __global__ void k_scatter(const Job* __restrict__ djob) {
     for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
         const TripEntry te = j.tscr[q];
         const int64_t e = te.unit / j.S;
-        const unsigned tag = (unsigned)((te.ijk >> kTagShift) & 3u);
+        const unsigned tag = (unsigned)((te.ijk >> kTagShift) & 7u);
         if (j.ev_class[e] != tag) continue;
         int32_t* r = j.triplets + 3 * (j.trip_off[te.unit] + te.rank);
         r[0] = (int32_t)(te.ijk & 0xfffffu);
@@ -1168,7 +1226,8 @@ __global__ void k_scatter(const Job* __restrict__ djob) {
 
 // ------------------------------------------------------------ launchers
 
-size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile); }
+size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile<SmallCfg>); }
+static size_t medium_smem_bytes() { return (size_t)MediumCfg::WPB * sizeof(WarpTile<MediumCfg>); }
 size_t heavy_smem_bytes() { return sizeof(HeavySmem); }
 
 static bool g_attr_done = false;
@@ -1181,6 +1240,10 @@ static cudaError_t ensure_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_light<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)light_smem_bytes(maxw));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_medium<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)medium_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_medium<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)medium_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
     if (e == cudaSuccess)
@@ -1202,6 +1265,15 @@ int heavy_max_blocks_per_sm() {
     if (ensure_attrs() != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heavy<false>, kHThreads, heavy_smem_bytes()) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int medium_max_blocks_per_sm() {
+    if (ensure_attrs() != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_medium<false>, 32 * MediumCfg::WPB, medium_smem_bytes()) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1231,6 +1303,7 @@ cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCf
 }
 
 cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
     k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
     k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
     k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
@@ -1257,6 +1330,7 @@ cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg
         const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
         k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
     }
+    k_medium<true><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
     k_heavy<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
     k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
     return cudaGetLastError();
