@@ -175,6 +175,39 @@ typedef struct {
 jpsi_status jpsi_timing_enable(jpsi_ctx *ctx, int enable);
 jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);
 
+/* ------------------------------------------------- allocation-free counting
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory while they run: for example a trigger
+ * process that reserves all of its GPU memory at start-up so that no
+ * cudaMalloc (which can synchronise the device and take milliseconds) ever
+ * lands in its latency budget, a plug-in running inside another program's
+ * event loop whose memory is owned by that program's allocator, or code that
+ * must not call cudaMalloc/cudaFree between its own stream operations.
+ *
+ * Counts passing triplets per unit and track candidates per event, exactly
+ * as jpsi_run does, without a context and without allocating: no cudaMalloc,
+ * cudaFree, host pinning or allocating library call.  Its only scratch is one
+ * file-scope device array of about 3.4 MB (job descriptor, control block and
+ * per-event bookkeeping for at most 262,144 events) that every GPU which loads
+ * the library holds until the process exits.
+ *   batch          device memory as for jpsi_run; n_events <= 262,144, else
+ *                  JPSI_EINVAL before anything runs.
+ *   track_counts   int32 [n_events] device, caller-owned (accept an event iff
+ *                  track_counts[e] >= min_candidates).
+ *   unit_counts    int32 [n_events * n_stations] device, caller-owned: passing
+ *                  triplets per unit (the counts jpsi_run scans into trip_off).
+ * Only events that fit the warp tiles (192 hits per layer, 384 per station, at
+ * most 64 passing trigger triplets in CHAIN mode, finite pruning bounds) are
+ * handled; a batch holding any other event returns JPSI_EINVAL (use jpsi_run).
+ * The call is synchronous on `cuda_stream`.  The first call on a device looks
+ * up the array's device address for that device (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (each call clears what must start at
+ * zero), so calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them. */
+jpsi_status jpsi_select_noalloc(const jpsi_params *params, const jpsi_batch *batch, int32_t *track_counts,
+                                int32_t *unit_counts, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *jpsi_strerror(jpsi_status status);
 

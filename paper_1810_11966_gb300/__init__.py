@@ -21,7 +21,7 @@ JPSI_MODE_PAPER, JPSI_MODE_CHAIN = 0, 1
 # every symbol include/jpsi.h declares
 EXPORTS = ("jpsi_create", "jpsi_destroy", "jpsi_run_plain", "jpsi_run", "jpsi_run_host", "jpsi_autotune",
            "jpsi_serve_start", "jpsi_serve_submit", "jpsi_serve_wait", "jpsi_serve_stop", "jpsi_strerror",
-           "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get")
+           "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get", "jpsi_select_noalloc")
 
 
 class JpsiError(RuntimeError):
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = False):
     lib.jpsi_timing_enable.restype = st
     lib.jpsi_timing_get.argtypes = [vp, P(jpsi_timing)]
     lib.jpsi_timing_get.restype = st
+    lib.jpsi_select_noalloc.argtypes = [P(jpsi_params), P(jpsi_batch), vp, vp, vp]
+    lib.jpsi_select_noalloc.restype = st
     _lib = lib
     return lib
 
@@ -172,6 +174,12 @@ def jpsi_timing_get(ctx) -> jpsi_timing:
     if s != JPSI_OK:
         raise JpsiError(s, "jpsi_timing_get")
     return t
+
+
+def jpsi_select_noalloc(params: jpsi_params, batch: jpsi_batch, track_counts, unit_counts, stream=0) -> int:
+    """Counting without allocation (see include/jpsi.h): device pointers for
+    track_counts [n_events] and unit_counts [n_events * n_stations]."""
+    return load().jpsi_select_noalloc(ctypes.byref(params), ctypes.byref(batch), track_counts, unit_counts, stream)
 
 
 # --------------------------------------------------------------- helpers

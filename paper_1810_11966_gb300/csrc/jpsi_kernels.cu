@@ -32,8 +32,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <mutex>
 
+#include "jpsi.h"
 #include "jpsi_device.cuh"
 #include "jpsi_internal.h"
 
@@ -1337,3 +1340,117 @@ cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg
 }
 
 }  // namespace jpsi
+
+// ======================================================================
+// Allocation-free counting entry point (jpsi_select_noalloc, include/jpsi.h).
+//
+// For callers that may not allocate device memory at run time.  Its only
+// scratch is the file-scope array below: the job descriptor, the control
+// block, one class byte per event and the three per-event lists of the warp
+// kernel, for at most kNoAllocMaxEvents events.  Every GPU that loads the
+// library holds the array until the process exits.  Host code must not use
+// the array's name as a device address: each device's address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+// ======================================================================
+namespace jpsi {
+
+constexpr int64_t kNoAllocMaxEvents = (int64_t)1 << 18;  // 262,144 events per call
+constexpr size_t kNoAllocJobOff = 0;
+constexpr size_t kNoAllocCtrlOff = 512;
+constexpr size_t kNoAllocClassOff = 1024;
+constexpr size_t kNoAllocListOff = kNoAllocClassOff + (size_t)kNoAllocMaxEvents;
+constexpr size_t kNoAllocBytes = kNoAllocListOff + 3 * sizeof(int32_t) * (size_t)kNoAllocMaxEvents;
+static_assert(sizeof(Job) <= kNoAllocCtrlOff - kNoAllocJobOff, "job descriptor slot");
+static_assert(sizeof(Ctrl) <= kNoAllocClassOff - kNoAllocCtrlOff, "control block slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_dev[kNoAllocMaxDevices];  // device address of the array, per device
+
+// Device address of the scratch array on `dev` (the current device).
+static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_dev[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *out = g_noalloc_dev[dev];
+    return cudaSuccess;
+}
+
+}  // namespace jpsi
+
+extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batch* b, int32_t* track_counts,
+                                           int32_t* unit_counts, void* cuda_stream) {
+    using namespace jpsi;
+    if (!p || !b) return JPSI_EINVAL;
+    if (p->n_stations < 1 || p->n_stations > kMaxStations || p->trigger_station < 0 ||
+        p->trigger_station >= p->n_stations || (p->mode != JPSI_MODE_PAPER && p->mode != JPSI_MODE_CHAIN) ||
+        p->ndf < 1 || p->min_candidates < 0 || !(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) ||
+        std::isinf(p->t_xz) || std::isinf(p->t_yz))
+        return JPSI_EINVAL;
+    const int64_t S = p->n_stations;
+    if (b->n_events < 0 || b->n_events > kNoAllocMaxEvents) return JPSI_EINVAL;  // beyond the static scratch
+    if (b->n_hits < 0 || b->n_hits >= ((int64_t)1 << 31) || (b->n_events == 0 && b->n_hits != 0)) return JPSI_EINVAL;
+    if (b->n_events == 0) return JPSI_OK;
+    if (!b->offsets || (b->n_hits > 0 && (!b->x || !b->y || !b->z)) || !track_counts || !unit_counts)
+        return JPSI_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return JPSI_ECUDA;
+    unsigned char* base = nullptr;
+    if (noalloc_scratch(dev, &base) != cudaSuccess) return JPSI_ECUDA;
+    Job* djob = reinterpret_cast<Job*>(base + kNoAllocJobOff);
+    Ctrl* dctrl = reinterpret_cast<Ctrl*>(base + kNoAllocCtrlOff);
+    Job j{};
+    j.x = b->x;
+    j.y = b->y;
+    j.z = b->z;
+    j.off = b->offsets;
+    j.n_events = b->n_events;
+    j.n_hits = b->n_hits;
+    j.S = p->n_stations;
+    j.trig = p->trigger_station;
+    j.mode = p->mode;
+    j.minc = p->min_candidates;
+    j.cx = (float)p->ndf * p->t_xz;
+    j.cy = (float)p->ndf * p->t_yz;
+    {  // pruning slope factor sqrt(max C)(1 + 1e-4) + 1e-20, rounded up (as for contexts)
+        const double kk = std::sqrt((double)std::max(j.cx, j.cy)) * (1.0 + 1e-4) + 1e-20;
+        float f = (float)kk;
+        if ((double)f < kk) f = std::nextafter(f, INFINITY);
+        j.K = f;
+    }
+    j.grab = 2;
+    j.unit_counts = unit_counts;
+    j.track_counts = track_counts;
+    j.ev_class = base + kNoAllocClassOff;
+    int32_t* lists = reinterpret_cast<int32_t*>(base + kNoAllocListOff);
+    j.mlist = lists;
+    j.hlist = lists + kNoAllocMaxEvents;
+    j.glist = lists + 2 * kNoAllocMaxEvents;
+    j.ctrl = dctrl;  // tlist, accept bits, offsets, triplets and entries stay null: the warp kernel alone runs
+    (void)S;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int n_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return JPSI_ECUDA;
+    const int wpb = 4;
+    const int per_sm = light_max_blocks_per_sm(wpb);
+    if (per_sm < 1) return JPSI_ECUDA;
+    if (cudaMemcpyAsync(djob, &j, sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess) return JPSI_ECUDA;
+    if (cudaMemsetAsync(dctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return JPSI_ECUDA;  // counters start at zero
+    k_light<false><<<n_sm * per_sm, 32 * wpb, light_smem_bytes(wpb), st>>>(djob, 1);
+    if (cudaGetLastError() != cudaSuccess) return JPSI_ECUDA;
+    Ctrl ctl{};
+    if (cudaMemcpyAsync(&ctl, dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return JPSI_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return JPSI_ECUDA;
+    if (ctl.status & kStInvalid) return JPSI_EINVAL;
+    // an event beyond the warp tile (or with extreme coordinates) needs the
+    // other kernels and their scratch: not available here
+    if (ctl.n_medium + ctl.n_heavy + ctl.n_generic > 0) return JPSI_EINVAL;
+    return JPSI_OK;
+}
+
