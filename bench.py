@@ -362,6 +362,57 @@ def run_serving(args, w, dev, jp, torch):
     ctx.close()
 
 
+def run_stress(args, w, dev, jp, torch):
+    """Combinatorial stress workload (6 stations, Poisson(1500) per layer,
+    window 1.0 cm): batches of at most 75 000 events (int32 CSR offsets), each
+    run once to size its triplet buffer and then timed; the triplet lists are
+    written in full."""
+    import synth
+    n_total = args.events or w.n_events
+    chunk = min(args.chunk, 75_000)
+    p = jp.params(**params_kw(args, w))
+    ctx = jp.Context(p, device=dev.index, hbm_budget=args.stress_budget_gb << 30)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    stream = torch.cuda.current_stream(dev)
+    tot_ms, trips, hits, gen_s = 0.0, 0, 0, 0.0
+    for e0 in range(0, n_total, chunk):
+        n = min(chunk, n_total - e0)
+        t0 = time.perf_counter()
+        b = synth.generate(w, e0, n)
+        gen_s += time.perf_counter() - t0
+        d = {k: torch.from_numpy(b[k]).to(dev) for k in ("x", "y", "z", "offsets")}
+        hits += b["n_hits"]
+        del b
+        batch = jp.make_batch(d["x"], d["y"], d["z"], d["offsets"], n, int(d["x"].numel()))
+        o = jp.jpsi_outputs()
+        acc = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        tc = torch.empty(n, dtype=torch.int32, device=dev)
+        toff = torch.empty(n * w.n_stations + 1, dtype=torch.int64, device=dev)
+        o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
+        ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))
+        trip = torch.empty((max(o.trip_needed, 1), 3), dtype=torch.int32, device=dev)
+        o.triplets, o.trip_capacity = trip.data_ptr(), o.trip_needed
+        ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))  # warm: sizes the triplet record
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e_a.record(stream)
+        ctx.check(jp.jpsi_run(ctx.ctx, batch, o, st))
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        tot_ms += e_a.elapsed_time(e_b)
+        trips += o.trip_needed
+        del d, trip, acc, tc, toff
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": n_total / (tot_ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "events": n_total, "chunk_events": chunk, "hits": hits,
+                       "stations": w.n_stations, "window_cm": w.window, "mode": args.mode},
+            "triplets": trips, "triplets_per_s": trips / (tot_ms / 1000), "generate_s": gen_s}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def params_kw(args, w):
     t = w.window ** 2
     return {"n_stations": w.n_stations, "mode": 1 if args.mode == "chain" else 0, "t_xz": t, "t_yz": t}
@@ -383,6 +434,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0, help="(for ncu) run this many steps and exit")
     ap.add_argument("--slices", type=int, default=None, help="timeslices (timeslice/stream workloads)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--chunk", type=int, default=50_000, help="events per batch (stress workload)")
+    ap.add_argument("--stress-budget-gb", type=int, default=160)
     ap.add_argument("--pool", type=int, default=8, help="distinct timeslices generated for the stream workload")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=int, default=16)
@@ -411,6 +464,8 @@ def main():
         return run_timeslices(args, w, dev, jp, torch)
     if w.name == "lognormal_stream":
         return run_serving(args, w, dev, jp, torch)
+    if w.name == "poisson1500_6st":
+        return run_stress(args, w, dev, jp, torch)
     n_ev = args.events or w.n_events
     S = w.n_stations
 
