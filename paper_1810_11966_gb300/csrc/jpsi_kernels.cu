@@ -145,6 +145,16 @@ __device__ __forceinline__ int owner_lane(int excl, int it) {
     return o;
 }
 
+// Pulls the hit lines [h0, h1) of x, y, z into L2 (addresses stay inside the
+// arrays: the first line starts at or after index h0 & ~31 >= 0).
+__device__ __forceinline__ void prefetch_hits_l2(const Job& j, int32_t h0, int32_t h1, int lane) {
+    for (int32_t a = (h0 & ~31) + 32 * lane; a < h1; a += 32 * 32) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.x + a));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.y + a));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.z + a));
+    }
+}
+
 __device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? trig : (si - 1 < trig ? si - 1 : si); }
 
 // ------------------------------------------------------- event offsets
@@ -654,6 +664,10 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         const bool to_medium = kSmall && fits_warp<MediumCfg>(j, o, nproc);
         if (lane == 0) push_event(j, e, to_medium ? kClsMedium : kClsHeavy);
         return;
+    }
+    {  // start every station's loads now: later stations stage from L2
+        const int s0 = j.mode == 1 ? 0 : j.trig, s1 = j.mode == 1 ? S : j.trig + 1;
+        prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s1), lane);
     }
     const TileView<NB> t{w.P, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
