@@ -9,6 +9,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -25,6 +26,8 @@ using namespace jpsi;
 namespace {
 
 constexpr size_t kDefaultBudget = (size_t)8 << 30;
+constexpr int kMaxChunks = 8;            // jpsi_run_host pipelines copies and counting in up to 8 chunks
+constexpr int64_t kChunkMinEvents = 65536;
 
 struct DevBuf {
     void* p = nullptr;
@@ -48,6 +51,9 @@ struct RunState {
     cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr, g_scatter = nullptr;
     int g_cfg_id = -1;
     cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
+    Job* d_jobs = nullptr;   // per-chunk jobs of the pipelined host run
+    Job* h_jobs = nullptr;   // pinned
+    cudaEvent_t chunk_ev[kMaxChunks] = {};
 };
 
 struct Slot {
@@ -82,6 +88,7 @@ struct jpsi_ctx {
     int grab = 2;
     int cfg_id = 0;  // bumps when the launch shape changes (graphs re-captured)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host-to-device copies of jpsi_run_host
     RunState rs;
     // device copies for jpsi_run_host
     DevBuf hx, hy, hz, hoff, hacc, htc, htoff, htrip;
@@ -229,6 +236,8 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.off = b->offsets;
     j.n_events = ne;
     j.n_hits = b->n_hits;
+    j.ev_begin = 0;
+    j.ev_count = ne;
     j.S = c->p.n_stations;
     j.trig = c->p.trigger_station;
     j.mode = c->p.mode;
@@ -289,6 +298,14 @@ void destroy_graphs(RunState& rs) {
 
 void state_free(jpsi_ctx* c, RunState& rs) {
     destroy_graphs(rs);
+    for (cudaEvent_t& e : rs.chunk_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (rs.d_jobs) cudaFree(rs.d_jobs);
+    if (rs.h_jobs) cudaFreeHost(rs.h_jobs);
+    rs.d_jobs = nullptr;
+    rs.h_jobs = nullptr;
     for (cudaEvent_t& e : rs.ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -508,6 +525,133 @@ jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_
     return s;
 }
 
+// jpsi_run_host for large batches: the hits go to the device chunk by chunk
+// on the copy stream while the warp kernels count the chunks that have
+// arrived (events [ev_begin, ev_begin + ev_count) of the batch); accept bits,
+// scan and triplet rows then run once over the whole batch.  Returns
+// JPSI_EBUSY (nothing done) when the batch is better run in one piece.
+jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_outputs* ho, cudaStream_t st) {
+    const int64_t S = c->p.n_stations, ne = hb->n_events, nu = ne * S, S3 = 3 * S;
+    const int nch = (int)std::min<int64_t>(kMaxChunks, ne / kChunkMinEvents);
+    if (nch < 2 || !c->copy_stream) return JPSI_EBUSY;
+    int64_t cs = (ne + nch - 1) / nch;
+    cs = (cs + 31) / 32 * 32;  // whole accept-bit words per chunk
+    const int32_t* hoff = hb->offsets;
+    for (int64_t e = 0; e <= ne; e += cs) {  // chunk boundaries must be usable as copy ranges
+        const int64_t b = hoff[std::min(e, ne) * S3];
+        if (b < 0 || b > hb->n_hits) return JPSI_EBUSY;
+    }
+    if (hoff[ne * S3] != hb->n_hits) return JPSI_EBUSY;
+    jpsi_status s;
+    if (!rs.d_jobs) {
+        if (cudaMalloc(&rs.d_jobs, sizeof(Job) * (kMaxChunks + 1)) != cudaSuccess ||
+            cudaMallocHost(&rs.h_jobs, sizeof(Job) * (kMaxChunks + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, JPSI_ENOMEM, "job slots");
+        }
+        for (cudaEvent_t& e : rs.chunk_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(c, JPSI_ECUDA, "events");
+    }
+    const size_t hbytes = (size_t)hb->n_hits * 4, obytes = (size_t)(ne * S3 + 1) * 4;
+    if ((s = ensure(c, c->hx, std::max<size_t>(hbytes, 4), "hits x")) || (s = ensure(c, c->hy, std::max<size_t>(hbytes, 4), "hits y")) ||
+        (s = ensure(c, c->hz, std::max<size_t>(hbytes, 4), "hits z")) || (s = ensure(c, c->hoff, obytes, "offsets")))
+        return s;
+    jpsi_batch db = *hb;
+    db.x = (const float*)c->hx.p;
+    db.y = (const float*)c->hy.p;
+    db.z = (const float*)c->hz.p;
+    db.offsets = (const int32_t*)c->hoff.p;
+    jpsi_outputs dout{};
+    if (ho->accept_bits) {
+        if ((s = ensure(c, c->hacc, (size_t)((ne + 31) / 32) * 4, "accept bits"))) return s;
+        dout.accept_bits = (uint32_t*)c->hacc.p;
+    }
+    if (ho->track_counts) {
+        if ((s = ensure(c, c->htc, (size_t)ne * 4, "track counts"))) return s;
+        dout.track_counts = (int32_t*)c->htc.p;
+    }
+    if (ho->trip_off || ho->triplets) {
+        if ((s = ensure(c, c->htoff, (size_t)(nu + 1) * 8, "triplet offsets"))) return s;
+        dout.trip_off = (int64_t*)c->htoff.p;
+    }
+    if (ho->triplets) {
+        if ((s = ensure(c, c->htrip, (size_t)std::max<int64_t>(ho->trip_capacity, 1) * 12, "triplets"))) return s;
+        dout.triplets = (int32_t*)c->htrip.p;
+        dout.trip_capacity = ho->trip_capacity;
+    }
+    if ((s = prepare(c, rs, &db, &dout)) != JPSI_OK) return s;
+    // every job descriptor goes first on the copy stream: a small copy queued
+    // on the compute stream would wait behind the hit copies in the copy engine
+    int k = 0;
+    for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
+        rs.h_jobs[k] = *rs.h_job;
+        rs.h_jobs[k].ev_begin = e0;
+        rs.h_jobs[k].ev_count = std::min(ne, e0 + cs) - e0;
+    }
+    const int njob = k;
+    rs.h_jobs[njob] = *rs.h_job;  // the whole batch (accept bits, scan, rows)
+    Job* d_all = rs.d_jobs + njob;
+    cudaError_t e = cudaMemcpyAsync(rs.d_jobs, rs.h_jobs, sizeof(Job) * (njob + 1), cudaMemcpyHostToDevice, c->copy_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hoff.p, hoff, obytes, cudaMemcpyHostToDevice, c->copy_stream);
+    k = 0;
+    for (int64_t e0 = 0; e0 < ne && e == cudaSuccess; e0 += cs, ++k) {
+        const int64_t e1 = std::min(ne, e0 + cs);
+        const int64_t h0 = hoff[e0 * S3], h1 = hoff[e1 * S3];
+        const size_t nb = (size_t)(h1 - h0) * 4;
+        if (nb) {
+            e = cudaMemcpyAsync((float*)c->hx.p + h0, hb->x + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync((float*)c->hy.p + h0, hb->y + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync((float*)c->hz.p + h0, hb->z + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(rs.chunk_ev[k], c->copy_stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "chunk upload");
+    const size_t ctr_off = offsetof(Ctrl, n_medium), ctr_len = offsetof(Ctrl, trip_total) - ctr_off;
+    if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
+    k = 0;
+    for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
+        const int64_t e1 = std::min(ne, e0 + cs);
+        if ((e = cudaStreamWaitEvent(st, rs.chunk_ev[k], 0)) != cudaSuccess ||
+            (k > 0 && (e = cudaMemsetAsync((char*)rs.d_ctrl + ctr_off, 0, ctr_len, st)) != cudaSuccess) ||
+            (e = launch_light_count(rs.d_jobs + k, e1 - e0, c->batch_cfg, true, st)) != cudaSuccess ||
+            (e = launch_count_lists(rs.d_jobs + k, c->batch_cfg, st)) != cudaSuccess)
+            return cuda_fail(c, e, "chunk count");
+    }
+    if ((e = launch_count_tail(d_all, c->batch_cfg, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "count phase");
+    const Ctrl ctl = *rs.h_ctrl;
+    if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
+    ho->trip_needed = ctl.trip_total;
+    s = JPSI_OK;
+    if (ho->triplets && ctl.trip_total > ho->trip_capacity) {
+        s = fail(c, JPSI_ECAPACITY, "triplet capacity " + std::to_string(ho->trip_capacity) + " < needed " +
+                                        std::to_string(ctl.trip_total));
+    } else if (ho->triplets && ctl.trip_total > 0) {
+        const bool scattered = rs.h_job->tscr && !(ctl.status & kStNoScratch) &&
+                               ctl.scratch_n <= (unsigned long long)rs.h_job->tscr_cap;
+        if (!scattered && rs.h_job->tscr && !(ctl.status & kStNoScratch))
+            rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
+        e = scattered ? launch_scatter(d_all, c->batch_cfg, st) : launch_emit_phase(d_all, ne, c->batch_cfg, true, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "emit");
+        if (rs.h_ctrl->status & kStEmitMismatch) return fail(c, JPSI_ECUDA, "internal: emit pass count mismatch");
+    }
+    e = cudaSuccess;
+    if (ho->accept_bits) e = cudaMemcpyAsync(ho->accept_bits, c->hacc.p, (size_t)((ne + 31) / 32) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->track_counts)
+        e = cudaMemcpyAsync(ho->track_counts, c->htc.p, (size_t)ne * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->trip_off)
+        e = cudaMemcpyAsync(ho->trip_off, c->htoff.p, (size_t)(nu + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ho->triplets && s == JPSI_OK && ctl.trip_total > 0)
+        e = cudaMemcpyAsync(ho->triplets, c->htrip.p, (size_t)ctl.trip_total * 12, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output download");
+    return s;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -552,8 +696,9 @@ jpsi_status jpsi_create(const jpsi_params* params, int device, size_t hbm_budget
     c->cx = (float)params->ndf * params->t_xz;
     c->cy = (float)params->ndf * params->t_yz;
     c->K = pruning_K(c->cx, c->cy);
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        jpsi_destroy(c);
         return JPSI_ECUDA;
     }
     if (state_init(c, c->rs) != JPSI_OK) {
@@ -576,6 +721,7 @@ void jpsi_destroy(jpsi_ctx* c) {
     DevBuf* bufs[] = {&c->hx, &c->hy, &c->hz, &c->hoff, &c->hacc, &c->htc, &c->htoff, &c->htrip};
     for (DevBuf* b : bufs) release(c, *b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
 }
 
@@ -609,6 +755,8 @@ jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, voi
     c->last_error.clear();
     jpsi_status s = check_batch(c, b, o, false);
     if (s != JPSI_OK) return s;
+    s = run_host_pipelined(c, c->rs, b, o, (cudaStream_t)stream);
+    if (s != JPSI_EBUSY) return s;
     return run_host_with(c, c->rs, b, o, c->hx, c->hy, c->hz, c->hoff, c->hacc, c->htc, c->htoff, c->htrip, -1,
                          (cudaStream_t)stream);
 }

@@ -48,8 +48,9 @@ struct Job {
     const float* y;
     const float* z;
     const int32_t* off;
-    int64_t n_events;
+    int64_t n_events;             // events of the whole batch
     int64_t n_hits;
+    int64_t ev_begin, ev_count;   // events the warp kernels take from the batch (all by default)
     int32_t S, trig, mode, minc;
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
@@ -88,6 +89,10 @@ struct LaunchCfg {
 cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st);
 cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+// The rest split in two, for counting a batch chunk by chunk: the medium,
+// block-tile and unpruned kernels (3 launches), then accept bits and scan (4).
+cudaError_t launch_count_lists(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_count_tail(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesLight = 1, kLaunchesRest = 7, kLaunchesEmit = 4;
 // Places the counting pass's triplet entries at trip_off[unit] + rank.
 cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st);

@@ -769,17 +769,18 @@ __global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, 
     const Cuts c{j.cx, j.cy, j.K};
     if (persistent) {
         unsigned long long* ctr = &j.ctrl->work[EMIT ? 4 : 0];
+        const long long e_end = j.ev_begin + j.ev_count;
         for (;;) {
             long long e0 = 0;
             if (lane == 0) e0 = (long long)atomicAdd(ctr, (unsigned long long)j.grab);
-            e0 = __shfl_sync(kFull, e0, 0);
-            if (e0 >= j.n_events) break;
-            const long long e1 = min(e0 + (long long)j.grab, (long long)j.n_events);
+            e0 = j.ev_begin + __shfl_sync(kFull, e0, 0);
+            if (e0 >= e_end) break;
+            const long long e1 = min(e0 + (long long)j.grab, e_end);
             for (long long e = e0; e < e1; ++e) light_event<EMIT, SmallCfg>(j, w, lane, c, e);
         }
     } else {
-        const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + wi;
-        if (e < j.n_events) light_event<EMIT, SmallCfg>(j, w, lane, c, e);
+        const long long e = j.ev_begin + (long long)blockIdx.x * (blockDim.x >> 5) + wi;
+        if (e < j.ev_begin + j.ev_count) light_event<EMIT, SmallCfg>(j, w, lane, c, e);
     }
 }
 
@@ -1330,6 +1331,21 @@ cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_count_lists(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
+    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
+    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_tail(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
+    k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
+    k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(djob);
+    k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
     k_scatter<<<lc.scan_blocks, 256, 0, st>>>(djob);
     return cudaGetLastError();
@@ -1426,6 +1442,8 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     j.off = b->offsets;
     j.n_events = b->n_events;
     j.n_hits = b->n_hits;
+    j.ev_begin = 0;
+    j.ev_count = b->n_events;
     j.S = p->n_stations;
     j.trig = p->trigger_station;
     j.mode = p->mode;

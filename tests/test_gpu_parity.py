@@ -265,3 +265,29 @@ def test_huge_layer_goes_unpruned(lib, oracle_mod):
     ref = _oracle(oracle_mod, 1, 1, 0.25, 0.25, b)
     assert ref["trip_needed"] >= 3
     assert_same(gpu_select(_ctx(lib, 1, 1), b), ref, 3)
+
+
+def test_run_host_pipelined_matches_device(lib, synth_mod):
+    # large enough that jpsi_run_host copies and counts in overlapping chunks
+    n = 300_001
+    b = synth_mod.generate("poisson20_1k", 0, n)
+    ctx = _ctx(lib)
+    dev = gpu_select(ctx, b)
+    acc = np.zeros((n + 31) // 32, np.uint32)
+    tc = np.zeros(n, np.int32)
+    to = np.zeros(n * 4 + 1, np.int64)
+    tr = np.zeros((dev["trip_needed"] + 1, 3), np.int32)
+    o = lib.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off, o.triplets = acc.ctypes.data, tc.ctypes.data, to.ctypes.data, tr.ctypes.data
+    o.trip_capacity = len(tr)
+    hb = lib.make_batch(b["x"], b["y"], b["z"], b["offsets"], n)
+    for _ in range(2):
+        s = lib.jpsi_run_host(ctx.ctx, hb, o, 0)
+        assert s == 0 and o.trip_needed == dev["trip_needed"]
+        host = {"status": 0, "trip_needed": o.trip_needed, "accept_bits": acc, "track_counts": tc, "trip_off": to,
+                "triplets": tr[: o.trip_needed]}
+        assert_same(host, dev, n * 4)
+    # too small a capacity: counts complete, ECAPACITY
+    o.trip_capacity = dev["trip_needed"] - 1
+    assert lib.jpsi_run_host(ctx.ctx, hb, o, 0) == lib.JPSI_ECAPACITY
+    assert o.trip_needed == dev["trip_needed"] and np.array_equal(tc, dev["track_counts"])
