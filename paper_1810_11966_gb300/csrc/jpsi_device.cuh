@@ -106,6 +106,26 @@ __device__ __forceinline__ HitPrep hit_prep(float x, float y, float z, float K) 
     return h;
 }
 
+// Fast staging path: slopes and bound without the per-hit classification.
+// ok is exactly live && !wild && !zbad of hit_prep: z in the normal range
+// [2^-126, 2^126) excludes z <= 0, NaN and Inf, and a finite b implies finite
+// s_x, s_y, hence finite x, y.
+struct HitFast {
+    float sx, sy, b;
+    bool ok;
+};
+
+__device__ __forceinline__ HitFast hit_fast(float x, float y, float z, float K) {
+    HitFast h;
+    float iz;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(z));
+    h.sx = __fmul_rn(x, iz);
+    h.sy = __fmul_rn(y, iz);
+    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, __fadd_rn(fabsf(h.sx), fabsf(h.sy)))), kTau);
+    h.ok = (z >= 1.17549435e-38f) & (z < 8.50705917e+37f) & (h.b < INFINITY);
+    return h;
+}
+
 // May hits i and j belong to one passing triplet?  (never false for such a pair)
 __device__ __forceinline__ bool pair_ok(float sxi, float syi, float bi, float sxj, float syj, float bj) {
     const float bb = __fadd_rn(bi, bj);
@@ -126,8 +146,9 @@ __device__ __forceinline__ bool tube_ok(float sx, float sy, float b, float mx, f
 // maps to a contiguous bin range.
 template <int NB>
 __device__ __forceinline__ int slope_bin(float v, float lo, float inv_w) {
-    const float t = floorf(__fmul_rn(__fsub_rn(v, lo), inv_w));
-    return (int)fminf(fmaxf(t, 0.0f), (float)(NB - 1));  // NaN -> 0 (only when inv_w = 0)
+    // floor to int saturates out-of-range values and maps NaN to 0
+    const int t = __float2int_rd(__fmul_rn(__fsub_rn(v, lo), inv_w));
+    return min(max(t, 0), NB - 1);
 }
 
 // Bins that contain every stored value v with |v - c| <= W (1 + 2^-20):

@@ -201,7 +201,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     float sx[R], sy[R], bb[R];
     bool lv[R];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
-    bool zbad = false, wild = false;
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) w.hist[BPL * lane + q] = 0;
 #pragma unroll
@@ -209,25 +209,47 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         lv[r] = false;
         sx[r] = sy[r] = bb[r] = 0.0f;
     }
+    // fast path: lanes past the end re-read the layer's last hit (a real hit,
+    // harmless in min/max; it is not stored)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;  // warp-uniform
         const int h = lane + 32 * r;
         const bool in = h < n;
-        const int hc = in ? h : n - 1;  // clamped: loads stay inside the layer
-        const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
-        zbad |= in & p.zbad;
-        wild |= in & p.wild;
-        lv[r] = in & p.live & !p.wild;
+        const int hc = in ? h : n - 1;
+        const HitFast p = hit_fast(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
+        bad |= !p.ok;
+        lv[r] = in;
         sx[r] = p.sx;
         sy[r] = p.sy;
         bb[r] = p.b;
-        lo = lv[r] ? fminf(lo, p.sx) : lo;
-        hi = lv[r] ? fmaxf(hi, p.sx) : hi;
-        bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
+        lo = fminf(lo, p.sx);
+        hi = fmaxf(hi, p.sx);
+        bmax = fmaxf(bmax, p.b);
     }
-    if (__any_sync(kFull, zbad)) return 1;
-    if (__any_sync(kFull, wild)) return 2;
+    if (__any_sync(kFull, bad)) {
+        // some hit has an odd coordinate: classify every hit exactly
+        bool zbad = false, wild = false;
+        lo = INFINITY;
+        hi = -INFINITY;
+        bmax = 0.0f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (32 * r >= n) break;
+            const int h = lane + 32 * r;
+            const bool in = h < n;
+            const int hc = in ? h : n - 1;
+            const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
+            zbad |= in & p.zbad;
+            wild |= in & p.wild;
+            lv[r] = in & p.live & !p.wild;
+            lo = lv[r] ? fminf(lo, p.sx) : lo;
+            hi = lv[r] ? fmaxf(hi, p.sx) : hi;
+            bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
+        }
+        if (__any_sync(kFull, zbad)) return 1;
+        if (__any_sync(kFull, wild)) return 2;
+    }
     lo = warp_min(lo);
     hi = warp_max(hi);
     bmax = warp_max(bmax);
