@@ -32,6 +32,20 @@ METRIC = "events/s on 1 GB300 (bit-exact accept bits), batched vs plain; p50/p99
 UNIT = "events/s"
 
 
+def shard(rank, n_per_rank):
+    """Events of one rank under torchrun: each rank owns its own contiguous
+    range of the workload's event stream (weak scaling, no data exchange)."""
+    return rank * n_per_rank, n_per_rank
+
+
+def max_over_ranks(value, dist):
+    """The slowest rank's time (the job's time): all-reduce MAX over gloo."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -471,10 +485,11 @@ def main():
 
     # host batch in pinned memory (for the end-to-end leg), then resident copies
     t0 = time.perf_counter()
-    counts = synth.layer_counts(w, rank * n_ev, n_ev)
+    e_first, _ = shard(rank, n_ev)
+    counts = synth.layer_counts(w, e_first, n_ev)
     n_hits = int(counts.sum())
     pin = {k: torch.empty(n_hits, dtype=torch.float32, pin_memory=True) for k in ("x", "y", "z")}
-    host = synth.generate(w, rank * n_ev, n_ev, out={k: v.numpy() for k, v in pin.items()})
+    host = synth.generate(w, e_first, n_ev, out={k: v.numpy() for k, v in pin.items()})
     off_pin = torch.from_numpy(host["offsets"]).pin_memory()
     gen_s = time.perf_counter() - t0
     d = {k: pin[k].to(dev) for k in ("x", "y", "z")}
@@ -523,9 +538,7 @@ def main():
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
         tot = evs[0].elapsed_time(evs[steps])
         if pg:
-            t = torch.tensor([tot], dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tot = float(t[0])
+            tot = max_over_ranks(tot, pg)
         return tot, per, tm
 
     clocks = Clocks(local)

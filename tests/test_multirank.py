@@ -1,0 +1,54 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks each take their own
+event range (no data exchange), synchronise with a barrier, and the job time is
+the maximum over ranks.  The oracle stands in for the GPU run here; the
+ranks' concatenated results must equal one run over all events."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, n_per_rank, out_dir):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+
+    import bench
+    import oracle
+    import synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    e0, n = bench.shard(rank, n_per_rank)
+    b = synth.generate("poisson20_1k", e0, n)
+    dist.barrier()
+    r = oracle.run(oracle.params(4, 1, t_xz=0.25), b, n_threads=1)
+    job = bench.max_over_ranks(10.0 * (rank + 1), dist)  # slowest rank's time
+    np.save(os.path.join(out_dir, f"tc{rank}.npy"), r["track_counts"])
+    np.save(os.path.join(out_dir, f"uc{rank}.npy"), r["unit_counts"])
+    with open(os.path.join(out_dir, f"job{rank}.txt"), "w") as f:
+        f.write(f"{e0} {n} {job}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_events(tmp_path, oracle_mod, synth_mod):
+    import torch.multiprocessing as mp
+    world, n = 2, 150
+    mp.start_processes(_rank_main, args=(world, _free_port(), n, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    jobs = [open(tmp_path / f"job{r}.txt").read().split() for r in range(world)]
+    assert [(int(a), int(b)) for a, b, _ in jobs] == [(0, n), (n, n)]      # disjoint, contiguous shards
+    assert all(float(j[2]) == 20.0 for j in jobs)                          # max over ranks, on every rank
+    tc = np.concatenate([np.load(tmp_path / f"tc{r}.npy") for r in range(world)])
+    uc = np.concatenate([np.load(tmp_path / f"uc{r}.npy") for r in range(world)])
+    whole = oracle_mod.run(oracle_mod.params(4, 1, t_xz=0.25), synth_mod.generate("poisson20_1k", 0, world * n))
+    assert np.array_equal(tc, whole["track_counts"]) and np.array_equal(uc, whole["unit_counts"])
