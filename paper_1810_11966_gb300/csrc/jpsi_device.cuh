@@ -19,7 +19,10 @@
 //     |s_i - s_j| <= b_i (1 - 5e-5) + b_j (1 - 5e-5),
 // so the FP32 test |fl(s_i - s_j)| <= fl(b_i + b_j) never rejects a pair that
 // belongs to a passing triplet (K's 1e-4 slack covers the error of r, kappa
-// the relative errors of s and eps |m|).  Hits with a non-finite coordinate
+// the relative errors of s and eps |m|).  The tiles keep one bound per layer,
+// B_l = max of b over the layer's stored hits, and test against
+// fl(B_l + B_l') >= fl(b_i + b_j) (rounding is monotone); the hits of a
+// detector layer share its z, so B_l is b up to the small kappa term.  Hits with a non-finite coordinate
 // cannot pass P1 at all (Szz, Suz or a residual becomes Inf/NaN) and are
 // dropped; hits with finite coordinates but z outside [2^-126, 2^126) or a
 // non-finite s or b send their event to the unpruned path.
@@ -126,9 +129,9 @@ __device__ __forceinline__ HitFast hit_fast(float x, float y, float z, float K) 
     return h;
 }
 
-// May hits i and j belong to one passing triplet?  (never false for such a pair)
-__device__ __forceinline__ bool pair_ok(float sxi, float syi, float bi, float sxj, float syj, float bj) {
-    const float bb = __fadd_rn(bi, bj);
+// May hits i and j belong to one passing triplet?  (never false for such a
+// pair when bb >= fl(b_i + b_j))
+__device__ __forceinline__ bool pair_ok(float sxi, float syi, float sxj, float syj, float bb) {
     return (fabsf(__fsub_rn(sxi, sxj)) <= bb) & (fabsf(__fsub_rn(syi, syj)) <= bb);
 }
 

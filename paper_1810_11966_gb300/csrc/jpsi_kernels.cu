@@ -68,37 +68,40 @@ constexpr int kHHCap = 6144;                      // hits per station tile
 constexpr int kNBH = 256;                         // slope bins per layer
 
 struct LayerMeta {
-    float lo, inv_w, bmax;
+    float lo, inv_w, bmax;  // bin map; bmax = largest pruning bound b of the layer
     int32_t base;   // global index of the layer's first hit
     int32_t pbase;  // tile position of the layer's first stored hit
     int32_t nlive;  // stored hits (finite coordinates)
 };
 
-// One station staged in shared memory: hits (s_x, s_y, b, layer-local index
-// as int bits) sorted by slope bin, bin starts and per-layer metadata.
+// One station staged in shared memory: hit slopes (s_x, s_y) and layer-local
+// indices, sorted by layer then slope bin; bin starts and per-layer metadata.
 template <int NB>
 struct TileView {
-    float4* P;
-    uint16_t* bst;  // [3][NB + 1] tile positions
+    float2* P;
+    uint16_t* idx;
+    uint16_t* bst;  // [3 * NB + 1] tile positions: layer l, bin b at l * NB + b
     LayerMeta* meta;
-    __device__ __forceinline__ int bin_start(int l, int b) const { return bst[l * (NB + 1) + b]; }
+    __device__ __forceinline__ int bin_start(int l, int b) const { return bst[l * NB + b]; }
 };
 
 template <class Cfg>
 struct WarpTile {
-    float4 P[Cfg::HCAP];
+    float2 P[Cfg::HCAP];
+    uint16_t idx[Cfg::HCAP];
     uint32_t queue[kQCap];
     float2 T[kTCap];            // trigger triplet slopes
     uint8_t alive[kTCap];
-    uint16_t bst[3 * (Cfg::NB + 1)];
+    uint16_t bst[3 * Cfg::NB + 1];
     LayerMeta meta[3];
     uint32_t hist[Cfg::NB];     // bin counts of the layer being staged
 };
 
 struct HeavySmem {
-    float4 P[kHHCap];
+    float2 P[kHHCap];
+    uint16_t idx[kHHCap];
     uint32_t queue[kHWarps][kQCap];
-    uint16_t bst[3 * (kNBH + 1)];
+    uint16_t bst[3 * kNBH + 1];
     LayerMeta meta[3];
     uint32_t hist[kNBH];
     int32_t off[3 * kMaxStations + 1];
@@ -198,7 +201,7 @@ template <class Cfg>
 __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t base, int32_t n, int32_t pbase,
                                 int lane, int& nlive) {
     constexpr int R = Cfg::RMAX, NB = Cfg::NB, BPL = NB / 32;  // bins per lane
-    float sx[R], sy[R], bb[R];
+    float sx[R], sy[R];
     bool lv[R];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool bad = false;
@@ -207,7 +210,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         lv[r] = false;
-        sx[r] = sy[r] = bb[r] = 0.0f;
+        sx[r] = sy[r] = 0.0f;
     }
     // fast path: lanes past the end re-read the layer's last hit (a real hit,
     // harmless in min/max; it is not stored)
@@ -222,7 +225,6 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         lv[r] = in;
         sx[r] = p.sx;
         sy[r] = p.sy;
-        bb[r] = p.b;
         lo = fminf(lo, p.sx);
         hi = fmaxf(hi, p.sx);
         bmax = fmaxf(bmax, p.b);
@@ -284,7 +286,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     }
     const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    uint16_t* bst = w.bst + l * (NB + 1);
+    uint16_t* bst = w.bst + l * NB;  // the end of layer l is the start of layer l + 1
     int run = pbase + incl - cnt;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
@@ -296,7 +298,11 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
-        if (lv[r]) w.P[bst[bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(lane + 32 * r));
+        if (lv[r]) {
+            const int pos = bst[bin[r]] + rank[r];
+            w.P[pos] = make_float2(sx[r], sy[r]);
+            w.idx[pos] = (uint16_t)(lane + 32 * r);
+        }
     }
     if (lane == 0) {
         LayerMeta m;
@@ -332,7 +338,7 @@ __device__ int stage_station_warp(const Job& j, WarpTile<Cfg>& w, int lane, cons
 __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t base, int32_t n, int32_t pbase,
                                  int& nlive) {
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    float sx[kHRMax], sy[kHRMax], bb[kHRMax];
+    float sx[kHRMax], sy[kHRMax];
     bool lv[kHRMax];
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
@@ -340,7 +346,7 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         lv[r] = false;
-        sx[r] = sy[r] = bb[r] = 0.0f;
+        sx[r] = sy[r] = 0.0f;
     }
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
@@ -354,7 +360,6 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         lv[r] = in & p.live & !p.wild;
         sx[r] = p.sx;
         sy[r] = p.sy;
-        bb[r] = p.b;
         lo = lv[r] ? fminf(lo, p.sx) : lo;
         hi = lv[r] ? fmaxf(hi, p.sx) : hi;
         bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
@@ -414,14 +419,18 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         woff += q < wp ? sm.wsum[q] : 0;
         total += sm.wsum[q];
     }
-    uint16_t* bst = sm.bst + l * (kNBH + 1);
+    uint16_t* bst = sm.bst + l * kNBH;  // the end of layer l is the start of layer l + 1
     bst[tid] = (uint16_t)(pbase + woff + incl - cnt);
     if (tid == kHThreads - 1) bst[kNBH] = (uint16_t)(pbase + total);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         if (kHThreads * r >= n) break;
-        if (lv[r]) sm.P[bst[bin[r]] + rank[r]] = make_float4(sx[r], sy[r], bb[r], __int_as_float(tid + kHThreads * r));
+        if (lv[r]) {
+            const int pos = bst[bin[r]] + rank[r];
+            sm.P[pos] = make_float2(sx[r], sy[r]);
+            sm.idx[pos] = (uint16_t)(tid + kHThreads * r);
+        }
     }
     if (tid == 0) {
         LayerMeta m;
@@ -466,7 +475,7 @@ struct TSink {
 template <bool EMIT, int NB>
 __device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
                       TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count) {
-    const float bmax2 = t.meta[2].bmax;
+    const float B02 = __fadd_rn(t.meta[0].bmax, t.meta[2].bmax), B12 = __fadd_rn(t.meta[1].bmax, t.meta[2].bmax);
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int q = q0 + lane;
@@ -474,10 +483,10 @@ __device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue
         int kb = 0, len = 0;
         if (q < qn) {
             en = queue[q];
-            const float4 Pi = t.P[en & 0xffffu], Pj = t.P[en >> 16];
+            const float2 Pi = t.P[en & 0xffffu], Pj = t.P[en >> 16];
             int a1, e1, a2, e2;
-            layer_range<NB>(t, 2, Pi.x, __fadd_rn(Pi.z, bmax2), a1, e1);
-            layer_range<NB>(t, 2, Pj.x, __fadd_rn(Pj.z, bmax2), a2, e2);
+            layer_range<NB>(t, 2, Pi.x, B02, a1, e1);
+            layer_range<NB>(t, 2, Pj.x, B12, a2, e2);
             kb = max(a1, a2);
             len = max(min(e1, e2) - kb, 0);
         }
@@ -494,11 +503,12 @@ __device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue
             float mx = 0.f, my = 0.f;
             int ii = 0, jj = 0, kk = 0;
             const bool in = it < total;
-            const float4 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[in ? ko : (int)(eo >> 16)];
-            if (in & pair_ok(Pi.x, Pi.y, Pi.z, Pk.x, Pk.y, Pk.z) & pair_ok(Pj.x, Pj.y, Pj.z, Pk.x, Pk.y, Pk.z)) {
-                ii = __float_as_int(Pi.w);
-                jj = __float_as_int(Pj.w);
-                kk = __float_as_int(Pk.w);
+            const int ko_c = in ? ko : (int)(eo >> 16);
+            const float2 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[ko_c];
+            if (in & pair_ok(Pi.x, Pi.y, Pk.x, Pk.y, B02) & pair_ok(Pj.x, Pj.y, Pk.x, Pk.y, B12)) {
+                ii = t.idx[eo & 0xffffu];
+                jj = t.idx[eo >> 16];
+                kk = t.idx[ko_c];
                 const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
                 const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
                 const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
@@ -562,13 +572,13 @@ __device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
     const int p0 = t.meta[0].pbase;
-    const float bmax1 = t.meta[1].bmax;
+    const float B01 = __fadd_rn(t.meta[0].bmax, t.meta[1].bmax);
     int qn = 0, count = 0;
     for (int i0 = 32 * warp; i0 < n0; i0 += 32 * nwarps) {
         const bool has = i0 + lane < n0;
-        const float4 Pi = t.P[p0 + (has ? i0 + lane : 0)];
+        const float2 Pi = t.P[p0 + (has ? i0 + lane : 0)];
         int jb, je;
-        layer_range<NB>(t, 1, Pi.x, __fadd_rn(Pi.z, bmax1), jb, je);
+        layer_range<NB>(t, 1, Pi.x, B01, jb, je);
         const int len = has ? je - jb : 0;
         const int incl = warp_incl_scan(len, lane);
         const int total = __shfl_sync(kFull, incl, 31);
@@ -579,9 +589,9 @@ __device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue
             const int o = owner_lane(excl, it);
             const int pj = __shfl_sync(kFull, shift, o) + it;
             const bool in = it < total;
-            const float4 Po = t.P[p0 + i0 + o];
-            const float4 Pj = t.P[in ? pj : p0];
-            const bool pass = in & pair_ok(Po.x, Po.y, Po.z, Pj.x, Pj.y, Pj.z);
+            const float2 Po = t.P[p0 + i0 + o];
+            const float2 Pj = t.P[in ? pj : p0];
+            const bool pass = in & pair_ok(Po.x, Po.y, Pj.x, Pj.y, B01);
             const unsigned mask = __ballot_sync(kFull, pass);
             if (mask) {
                 if (pass) queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
@@ -608,22 +618,23 @@ __device__ bool road(const Job& j, const TileView<NB>& t, const Cuts& c, float m
     for (int l = 0; l < 3; ++l)
         layer_range<NB>(t, l, mx, __fadd_rn(t.meta[l].bmax, __fmul_rn(2.0f * kKappa, fabsf(mx))), a[l], e[l]);
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
+    const float b0 = t.meta[0].bmax, b1 = t.meta[1].bmax, b2 = t.meta[2].bmax;
     for (int p0 = a[0]; p0 < e[0]; ++p0) {
-        const float4 P0 = t.P[p0];
-        if (!tube_ok(P0.x, P0.y, P0.z, mx, my)) continue;
-        const int h0 = base0 + __float_as_int(P0.w);
+        const float2 P0 = t.P[p0];
+        if (!tube_ok(P0.x, P0.y, b0, mx, my)) continue;
+        const int h0 = base0 + t.idx[p0];
         const float x0 = __ldg(j.x + h0), y0 = __ldg(j.y + h0), z0 = __ldg(j.z + h0);
         if (!tube_pass(x0, y0, z0, mx, my, c)) continue;
         for (int p1 = a[1]; p1 < e[1]; ++p1) {
-            const float4 P1 = t.P[p1];
-            if (!tube_ok(P1.x, P1.y, P1.z, mx, my)) continue;
-            const int h1 = base1 + __float_as_int(P1.w);
+            const float2 P1 = t.P[p1];
+            if (!tube_ok(P1.x, P1.y, b1, mx, my)) continue;
+            const int h1 = base1 + t.idx[p1];
             const float x1 = __ldg(j.x + h1), y1 = __ldg(j.y + h1), z1 = __ldg(j.z + h1);
             if (!tube_pass(x1, y1, z1, mx, my, c)) continue;
             for (int p2 = a[2]; p2 < e[2]; ++p2) {
-                const float4 P2 = t.P[p2];
-                if (!tube_ok(P2.x, P2.y, P2.z, mx, my)) continue;
-                const int h2 = base2 + __float_as_int(P2.w);
+                const float2 P2 = t.P[p2];
+                if (!tube_ok(P2.x, P2.y, b2, mx, my)) continue;
+                const int h2 = base2 + t.idx[p2];
                 const float xs[3] = {x0, x1, __ldg(j.x + h2)};
                 const float ys[3] = {y0, y1, __ldg(j.y + h2)};
                 const float zs[3] = {z0, z1, __ldg(j.z + h2)};
@@ -691,7 +702,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         const int s0 = j.mode == 1 ? 0 : j.trig, s1 = j.mode == 1 ? S : j.trig + 1;
         prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s1), lane);
     }
-    const TileView<NB> t{w.P, w.bst, w.meta};
+    const TileView<NB> t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
@@ -755,7 +766,7 @@ __device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const
     if (!any) return;
     EvOff o;
     warp_load_offsets(j, e, lane, o);
-    const TileView<NB> t{w.P, w.bst, w.meta};
+    const TileView<NB> t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, nullptr, 0, nullptr, 0};
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
@@ -868,7 +879,7 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t 
             return;
         }
     }
-    const TileView<kNBH> t{sm.P, sm.bst, sm.meta};
+    const TileView<kNBH> t{sm.P, sm.idx, sm.bst, sm.meta};
     float2* T = j.tlist + (int64_t)blockIdx.x * j.tlist_cap;
     uint8_t* alive = j.talive + (int64_t)blockIdx.x * j.tlist_cap;
     int trig_count = 0, nT = 0;
@@ -949,7 +960,7 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t 
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(kHThreads, 2) k_heavy(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(kHThreads, 3) k_heavy(const Job* __restrict__ djob) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
     const Job j = *djob;
@@ -1066,13 +1077,16 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
                 const int64_t i = p / n1, jx = p - i * n1;
                 const GHit hi = ghit(j, o[0] + i), hj = ghit(j, o[1] + jx);
                 if (!hi.p.live || !hj.p.live) continue;
-                if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hi.p.b, hj.p.sx, hj.p.sy, hj.p.b)) continue;
+                if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hj.p.sx, hj.p.sy, __fadd_rn(hi.p.b, hj.p.b)))
+                    continue;
                 for (int64_t k = 0; k < n2; ++k) {
                     const GHit hk = ghit(j, o[2] + k);
                     if (!hk.p.live) continue;
                     if (!hk.p.wild) {
-                        if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hi.p.b, hk.p.sx, hk.p.sy, hk.p.b)) continue;
-                        if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hj.p.b, hk.p.sx, hk.p.sy, hk.p.b)) continue;
+                        if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hi.p.b, hk.p.b)))
+                            continue;
+                        if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hj.p.b, hk.p.b)))
+                            continue;
                     }
                     const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
                     float mx, my;
