@@ -39,21 +39,28 @@ struct HostBuf {
     size_t bytes = 0;
 };
 
-// Per-run device state: job descriptor, control block, graphs.  The serving
-// loop owns one per slot; plain runs use the context's own.
+// One captured phase of the batched form: the graph (kept for its kernel
+// node handles), its executable form and each kernel node's launch shape,
+// re-applied with the current job before every replay.
+struct Graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+    std::vector<cudaKernelNodeParams> params;
+};
+
+// Per-run state: job, control block, graphs.  The serving loop owns one per
+// slot; plain runs use the context's own.
 struct RunState {
-    Job* d_job = nullptr;
-    Job* h_job = nullptr;     // pinned
+    Job job{};                // the current run's job (passed to every kernel by value)
     Ctrl* d_ctrl = nullptr;
     Ctrl* h_ctrl = nullptr;   // pinned
     DevBuf unit_counts, track_counts, ev_class, mlist, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
-    cudaGraphExec_t g_light = nullptr, g_rest = nullptr, g_emit = nullptr, g_scatter = nullptr;
+    Graph g_light, g_rest, g_emit, g_scatter;
     int g_cfg_id = -1;
     cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
-    Job* d_jobs = nullptr;   // per-chunk jobs of the pipelined host run
-    Job* h_jobs = nullptr;   // pinned
-    cudaEvent_t chunk_ev[kMaxChunks] = {};
+    cudaEvent_t chunk_ev[kMaxChunks] = {};  // hit chunks copied (pipelined host run)
 };
 
 struct Slot {
@@ -229,7 +236,8 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     if (!o->track_counts && (st = ensure(c, rs.track_counts, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts")))
         return st;
     if (!o->trip_off && (st = ensure(c, rs.trip_off, (size_t)(nu + 1) * 8, "triplet offsets"))) return st;
-    Job& j = *rs.h_job;
+    Job& j = rs.job;
+    j = Job{};
     j.x = b->x;
     j.y = b->y;
     j.z = b->z;
@@ -276,12 +284,11 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
 }
 
 jpsi_status state_init(jpsi_ctx* c, RunState& rs) {
-    if (cudaMalloc(&rs.d_job, sizeof(Job)) != cudaSuccess || cudaMalloc(&rs.d_ctrl, sizeof(Ctrl)) != cudaSuccess ||
-        cudaMallocHost(&rs.h_job, sizeof(Job)) != cudaSuccess || cudaMallocHost(&rs.h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    if (cudaMalloc(&rs.d_ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMallocHost(&rs.h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, JPSI_ENOMEM, "control block allocation failed");
     }
-    memset(rs.h_job, 0, sizeof(Job));
+    rs.job = Job{};
     memset(rs.h_ctrl, 0, sizeof(Ctrl));
     for (cudaEvent_t& e : rs.ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(c, JPSI_ECUDA, "event creation failed");
@@ -289,10 +296,11 @@ jpsi_status state_init(jpsi_ctx* c, RunState& rs) {
 }
 
 void destroy_graphs(RunState& rs) {
-    cudaGraphExec_t* gs[] = {&rs.g_light, &rs.g_rest, &rs.g_emit, &rs.g_scatter};
-    for (cudaGraphExec_t* g : gs) {
-        if (*g) cudaGraphExecDestroy(*g);
-        *g = nullptr;
+    Graph* gs[] = {&rs.g_light, &rs.g_rest, &rs.g_emit, &rs.g_scatter};
+    for (Graph* g : gs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->g) cudaGraphDestroy(g->g);
+        *g = Graph{};
     }
 }
 
@@ -302,21 +310,13 @@ void state_free(jpsi_ctx* c, RunState& rs) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
-    if (rs.d_jobs) cudaFree(rs.d_jobs);
-    if (rs.h_jobs) cudaFreeHost(rs.h_jobs);
-    rs.d_jobs = nullptr;
-    rs.h_jobs = nullptr;
     for (cudaEvent_t& e : rs.ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
-    if (rs.d_job) cudaFree(rs.d_job);
     if (rs.d_ctrl) cudaFree(rs.d_ctrl);
-    if (rs.h_job) cudaFreeHost(rs.h_job);
     if (rs.h_ctrl) cudaFreeHost(rs.h_ctrl);
-    rs.d_job = nullptr;
     rs.d_ctrl = nullptr;
-    rs.h_job = nullptr;
     rs.h_ctrl = nullptr;
     release(c, rs.unit_counts);
     release(c, rs.track_counts);
@@ -331,34 +331,56 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.tscr);
 }
 
-// Captures the count and emit phases of the batched form into graphs that
-// read their job from rs.d_job (valid for every batch).
+// Captures the count and emit phases of the batched form into graphs (with
+// the current job; graph_launch writes each run's job into their nodes).
 jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
-    if (rs.g_light && rs.g_cfg_id == c->cfg_id) return JPSI_OK;
+    if (rs.g_light.exec && rs.g_cfg_id == c->cfg_id) return JPSI_OK;
     std::lock_guard<std::mutex> cap_lock(c->cap_mu);
     destroy_graphs(rs);
     for (int phase = 0; phase < 4; ++phase) {
-        cudaGraph_t g = nullptr;
+        Graph& G = phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : phase == 2 ? rs.g_emit : rs.g_scatter;
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
-        cudaError_t le = phase == 0   ? launch_light_count(rs.d_job, 0, c->batch_cfg, true, c->cap_stream)
-                         : phase == 1 ? launch_count_rest(rs.d_job, c->batch_cfg, c->cap_stream)
-                         : phase == 2 ? launch_emit_phase(rs.d_job, 0, c->batch_cfg, true, c->cap_stream)
-                                      : launch_scatter(rs.d_job, c->batch_cfg, c->cap_stream);
-        e = cudaStreamEndCapture(c->cap_stream, &g);
-        if (le != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return cuda_fail(c, le, "graph capture launch");
-        }
+        cudaError_t le = phase == 0   ? launch_light_count(rs.job, 0, c->batch_cfg, true, c->cap_stream)
+                         : phase == 1 ? launch_count_rest(rs.job, c->batch_cfg, c->cap_stream)
+                         : phase == 2 ? launch_emit_phase(rs.job, 0, c->batch_cfg, true, c->cap_stream)
+                                      : launch_scatter(rs.job, c->batch_cfg, c->cap_stream);
+        e = cudaStreamEndCapture(c->cap_stream, &G.g);
+        if (le != cudaSuccess) return cuda_fail(c, le, "graph capture launch");
         if (e != cudaSuccess) return cuda_fail(c, e, "graph end capture");
-        cudaGraphExec_t ge = nullptr;
-        e = cudaGraphInstantiate(&ge, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-        (phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : phase == 2 ? rs.g_emit : rs.g_scatter) = ge;
+        size_t n = 0;
+        if ((e = cudaGraphGetNodes(G.g, nullptr, &n)) != cudaSuccess) return cuda_fail(c, e, "graph nodes");
+        std::vector<cudaGraphNode_t> all(n);
+        if (n && (e = cudaGraphGetNodes(G.g, all.data(), &n)) != cudaSuccess) return cuda_fail(c, e, "graph nodes");
+        for (cudaGraphNode_t node : all) {
+            cudaGraphNodeType t;
+            if ((e = cudaGraphNodeGetType(node, &t)) != cudaSuccess) return cuda_fail(c, e, "graph node type");
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp{};
+            if ((e = cudaGraphKernelNodeGetParams(node, &kp)) != cudaSuccess) return cuda_fail(c, e, "graph node");
+            G.nodes.push_back(node);
+            G.params.push_back(kp);
+        }
+        if ((e = cudaGraphInstantiate(&G.exec, G.g, 0)) != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     }
     rs.g_cfg_id = c->cfg_id;
     return JPSI_OK;
+}
+
+// Replays a captured phase for `job`: every kernel node of the graph takes
+// the job as its only parameter (warp kernels in their persistent form).
+cudaError_t graph_launch(Graph& G, const Job& job, cudaStream_t st) {
+    Job j = job;
+    j.persistent = 1;
+    void* args[] = {&j};
+    for (size_t i = 0; i < G.nodes.size(); ++i) {
+        cudaKernelNodeParams kp = G.params[i];
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        const cudaError_t e = cudaGraphExecKernelNodeSetParams(G.exec, G.nodes[i], &kp);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGraphLaunch(G.exec, st);
 }
 
 // Accumulates per-phase device times of a finished run (events already complete).
@@ -383,16 +405,14 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     if ((s = prepare(c, rs, b, o)) != JPSI_OK) return s;
     const int64_t ne = b->n_events, nu = ne * c->p.n_stations;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(rs.d_job, rs.h_job, sizeof(Job), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(c, e, "job upload");
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
     const bool timing = c->timing.load();
     if (batched && (s = capture_graphs(c, rs)) != JPSI_OK) return s;
     if (timing) cudaEventRecord(rs.ev[0], st);
-    e = batched ? cudaGraphLaunch(rs.g_light, st) : launch_light_count(rs.d_job, ne, c->plain_cfg, false, st);
+    e = batched ? graph_launch(rs.g_light, rs.job, st) : launch_light_count(rs.job, ne, c->plain_cfg, false, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "light count");
     if (timing) cudaEventRecord(rs.ev[1], st);
-    e = batched ? cudaGraphLaunch(rs.g_rest, st) : launch_count_rest(rs.d_job, c->plain_cfg, st);
+    e = batched ? graph_launch(rs.g_rest, rs.job, st) : launch_count_rest(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "count rest");
     if (timing) cudaEventRecord(rs.ev[2], st);
     int launches = kLaunchesLight + kLaunchesRest;
@@ -416,15 +436,15 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     }
     // triplet rows: scatter the recorded entries, or re-enumerate when they
     // did not fit (then record more next time, within the budget)
-    const bool scattered = rs.h_job->tscr && !(ctl.status & kStNoScratch) &&
-                           ctl.scratch_n <= (unsigned long long)rs.h_job->tscr_cap;
-    if (!scattered && rs.h_job->tscr && !(ctl.status & kStNoScratch))
+    const bool scattered = rs.job.tscr && !(ctl.status & kStNoScratch) &&
+                           ctl.scratch_n <= (unsigned long long)rs.job.tscr_cap;
+    if (!scattered && rs.job.tscr && !(ctl.status & kStNoScratch))
         rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
     if (timing) cudaEventRecord(rs.ev[3], st);
     if (scattered)
-        e = batched ? cudaGraphLaunch(rs.g_scatter, st) : launch_scatter(rs.d_job, c->plain_cfg, st);
+        e = batched ? graph_launch(rs.g_scatter, rs.job, st) : launch_scatter(rs.job, c->plain_cfg, st);
     else
-        e = batched ? cudaGraphLaunch(rs.g_emit, st) : launch_emit_phase(rs.d_job, ne, c->plain_cfg, false, st);
+        e = batched ? graph_launch(rs.g_emit, rs.job, st) : launch_emit_phase(rs.job, ne, c->plain_cfg, false, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "emit");
     if (timing) cudaEventRecord(rs.ev[4], st);
     launches += scattered ? kLaunchesScatter : kLaunchesEmit;
@@ -543,12 +563,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
     }
     if (hoff[ne * S3] != hb->n_hits) return JPSI_EBUSY;
     jpsi_status s;
-    if (!rs.d_jobs) {
-        if (cudaMalloc(&rs.d_jobs, sizeof(Job) * (kMaxChunks + 1)) != cudaSuccess ||
-            cudaMallocHost(&rs.h_jobs, sizeof(Job) * (kMaxChunks + 1)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, JPSI_ENOMEM, "job slots");
-        }
+    if (!rs.chunk_ev[0]) {
         for (cudaEvent_t& e : rs.chunk_ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(c, JPSI_ECUDA, "events");
     }
@@ -580,20 +595,9 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         dout.trip_capacity = ho->trip_capacity;
     }
     if ((s = prepare(c, rs, &db, &dout)) != JPSI_OK) return s;
-    // every job descriptor goes first on the copy stream: a small copy queued
-    // on the compute stream would wait behind the hit copies in the copy engine
+    const Job& all = rs.job;  // the whole batch (accept bits, scan, rows)
+    cudaError_t e = cudaMemcpyAsync(c->hoff.p, hoff, obytes, cudaMemcpyHostToDevice, c->copy_stream);
     int k = 0;
-    for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
-        rs.h_jobs[k] = *rs.h_job;
-        rs.h_jobs[k].ev_begin = e0;
-        rs.h_jobs[k].ev_count = std::min(ne, e0 + cs) - e0;
-    }
-    const int njob = k;
-    rs.h_jobs[njob] = *rs.h_job;  // the whole batch (accept bits, scan, rows)
-    Job* d_all = rs.d_jobs + njob;
-    cudaError_t e = cudaMemcpyAsync(rs.d_jobs, rs.h_jobs, sizeof(Job) * (njob + 1), cudaMemcpyHostToDevice, c->copy_stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hoff.p, hoff, obytes, cudaMemcpyHostToDevice, c->copy_stream);
-    k = 0;
     for (int64_t e0 = 0; e0 < ne && e == cudaSuccess; e0 += cs, ++k) {
         const int64_t e1 = std::min(ne, e0 + cs);
         const int64_t h0 = hoff[e0 * S3], h1 = hoff[e1 * S3];
@@ -611,13 +615,16 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
     k = 0;
     for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
         const int64_t e1 = std::min(ne, e0 + cs);
+        Job jk = all;  // the chunk's events
+        jk.ev_begin = e0;
+        jk.ev_count = e1 - e0;
         if ((e = cudaStreamWaitEvent(st, rs.chunk_ev[k], 0)) != cudaSuccess ||
             (k > 0 && (e = cudaMemsetAsync((char*)rs.d_ctrl + ctr_off, 0, ctr_len, st)) != cudaSuccess) ||
-            (e = launch_light_count(rs.d_jobs + k, e1 - e0, c->batch_cfg, true, st)) != cudaSuccess ||
-            (e = launch_count_lists(rs.d_jobs + k, c->batch_cfg, st)) != cudaSuccess)
+            (e = launch_light_count(jk, e1 - e0, c->batch_cfg, true, st)) != cudaSuccess ||
+            (e = launch_count_lists(jk, c->batch_cfg, st)) != cudaSuccess)
             return cuda_fail(c, e, "chunk count");
     }
-    if ((e = launch_count_tail(d_all, c->batch_cfg, st)) != cudaSuccess ||
+    if ((e = launch_count_tail(all, c->batch_cfg, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(c, e, "count phase");
@@ -629,11 +636,11 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         s = fail(c, JPSI_ECAPACITY, "triplet capacity " + std::to_string(ho->trip_capacity) + " < needed " +
                                         std::to_string(ctl.trip_total));
     } else if (ho->triplets && ctl.trip_total > 0) {
-        const bool scattered = rs.h_job->tscr && !(ctl.status & kStNoScratch) &&
-                               ctl.scratch_n <= (unsigned long long)rs.h_job->tscr_cap;
-        if (!scattered && rs.h_job->tscr && !(ctl.status & kStNoScratch))
+        const bool scattered = all.tscr && !(ctl.status & kStNoScratch) &&
+                               ctl.scratch_n <= (unsigned long long)all.tscr_cap;
+        if (!scattered && all.tscr && !(ctl.status & kStNoScratch))
             rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
-        e = scattered ? launch_scatter(d_all, c->batch_cfg, st) : launch_emit_phase(d_all, ne, c->batch_cfg, true, st);
+        e = scattered ? launch_scatter(all, c->batch_cfg, st) : launch_emit_phase(all, ne, c->batch_cfg, true, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "emit");

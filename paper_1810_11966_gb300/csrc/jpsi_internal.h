@@ -41,8 +41,9 @@ struct Ctrl {
     unsigned long long scratch_n; // triplet entries appended by the counting pass
 };
 
-// Everything a run's kernels read; lives in device memory so a captured
-// graph can be replayed for any batch after the host rewrites it.
+// Everything a run's kernels read.  Kernels take it by value (a
+// __grid_constant__ parameter); a captured graph gets the current job
+// written into its kernel nodes before each replay.
 struct Job {
     const float* x;
     const float* y;
@@ -54,6 +55,7 @@ struct Job {
     int32_t S, trig, mode, minc;
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
+    int32_t persistent;           // warp kernels: persistent warps (1) or one warp per event (0)
     int32_t* unit_counts;         // [n_events*S]
     int32_t* track_counts;        // [n_events]
     uint8_t* ev_class;            // [n_events]: kCls*
@@ -86,20 +88,20 @@ struct LaunchCfg {
 // Count phase = small warp kernel, then the rest (medium warp kernel,
 // block-tile kernel, unpruned block kernel, accept bits, scan).  Kernel
 // launches per call: 1 and 7.
-cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+cudaError_t launch_light_count(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st);
-cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 // The rest split in two, for counting a batch chunk by chunk: the medium,
 // block-tile and unpruned kernels (3 launches), then accept bits and scan (4).
-cudaError_t launch_count_lists(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
-cudaError_t launch_count_tail(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesLight = 1, kLaunchesRest = 7, kLaunchesEmit = 4;
 // Places the counting pass's triplet entries at trip_off[unit] + rank.
-cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesScatter = 1;
 // Emit phase (fallback when the entries overflowed): the three kernels
 // re-enumerate their units and write rows at trip_off.
-cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+cudaError_t launch_emit_phase(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                               cudaStream_t st);
 size_t light_smem_bytes(int wpb);
 int light_max_blocks_per_sm(int wpb);

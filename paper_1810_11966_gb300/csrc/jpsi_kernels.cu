@@ -794,13 +794,12 @@ __device__ __forceinline__ void light_event(const Job& j, WarpTile<Cfg>& w, int 
 // Small warp tiles: every event of the batch (statically one warp per event,
 // or persistent warps grabbing `grab` events at a time).
 template <bool EMIT>
-__global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, int persistent) {
+__global__ void __launch_bounds__(256, 4) k_light(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Job j = *djob;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     WarpTile<SmallCfg>& w = reinterpret_cast<WarpTile<SmallCfg>*>(smem_raw)[wi];
     const Cuts c{j.cx, j.cy, j.K};
-    if (persistent) {
+    if (j.persistent) {
         unsigned long long* ctr = &j.ctrl->work[EMIT ? 4 : 0];
         const long long e_end = j.ev_begin + j.ev_count;
         for (;;) {
@@ -820,9 +819,8 @@ __global__ void __launch_bounds__(256, 4) k_light(const Job* __restrict__ djob, 
 // Medium warp tiles: the events the small tiles passed on, one at a time per
 // warp from the medium list.
 template <bool EMIT>
-__global__ void __launch_bounds__(128, 3) k_medium(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(128, 3) k_medium(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Job j = *djob;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     WarpTile<MediumCfg>& w = reinterpret_cast<WarpTile<MediumCfg>*>(smem_raw)[wi];
     const Cuts c{j.cx, j.cy, j.K};
@@ -960,10 +958,9 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t 
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(kHThreads, 3) k_heavy(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(kHThreads, 3) k_heavy(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
-    const Job j = *djob;
     const Cuts c{j.cx, j.cy, j.K};
     const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
     for (;;) {
@@ -1023,10 +1020,9 @@ __device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, fl
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(256) k_generic(const __grid_constant__ Job j) {
     __shared__ int32_t soff[3 * kMaxStations + 1];
     __shared__ int s_gi, s_count, s_cand, s_bad;
-    const Job j = *djob;
     const Cuts c{j.cx, j.cy, j.K};
     const int n_gen = *(volatile int32_t*)&j.ctrl->n_generic;
     const int S = j.S, S3 = 3 * S;
@@ -1145,8 +1141,7 @@ __global__ void __launch_bounds__(256) k_generic(const Job* __restrict__ djob) {
 
 // -------------------------------------------------------- accept bits
 
-__global__ void k_accept(const Job* __restrict__ djob) {
-    const Job j = *djob;
+__global__ void k_accept(const __grid_constant__ Job j) {
     if (!j.accept_bits) return;
     const int64_t nwords = (j.n_events + 31) / 32;
     const int lane = threadIdx.x & 31;
@@ -1195,9 +1190,8 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64
     return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const __grid_constant__ Job j) {
     __shared__ int64_t sh[33];
-    const Job j = *djob;
     const int64_t n = j.n_events * j.S;
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -1212,9 +1206,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Job* __restr
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(const __grid_constant__ Job j) {
     __shared__ int64_t sh[33];
-    const Job j = *djob;
     const int64_t n = j.n_events * j.S;
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     int64_t carry = 0;
@@ -1232,9 +1225,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(const Job* __restrict
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const Job* __restrict__ djob) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const __grid_constant__ Job j) {
     __shared__ int64_t sh[33];
-    const Job j = *djob;
     const int64_t n = j.n_events * j.S;
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -1262,8 +1254,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Job* __restric
 // Moves each recorded triplet to its row trip_off[unit] + rank.  Entries
 // written by a path that did not keep the event (it moved on to the next
 // path part-way) are dropped; the final path recorded the event again.
-__global__ void k_scatter(const Job* __restrict__ djob) {
-    const Job j = *djob;
+__global__ void k_scatter(const __grid_constant__ Job j) {
     const unsigned long long n = j.ctrl->scratch_n;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
@@ -1341,67 +1332,59 @@ int generic_max_blocks_per_sm(int threads) {
 
 const void* light_count_kernel_ptr() { return (const void*)k_light<false>; }
 
-cudaError_t launch_light_count(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+// Kernels take the job by value (a __grid_constant__ parameter), so every
+// field read is a constant-bank operand rather than a load.
+cudaError_t launch_light_count(const Job& job, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st) {
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     const int wpb = lc.light_wpb;
     const size_t smem = light_smem_bytes(wpb);
-    if (persistent) {
-        k_light<false><<<lc.light_blocks, wpb * 32, smem, st>>>(djob, 1);
-    } else {
-        const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
-        k_light<false><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
-    }
+    Job j = job;
+    j.persistent = persistent ? 1 : 0;
+    const int64_t nb = persistent ? lc.light_blocks : std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
+    k_light<false><<<(unsigned)nb, wpb * 32, smem, st>>>(j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_rest(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
-    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
-    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
-    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
-    k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
-    k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(djob);
-    k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
+    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_lists(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
-    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
-    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
-    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
+cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    k_accept<<<lc.scan_blocks, 256, 0, st>>>(j);
+    k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(j);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(j);
+    k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_tail(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
-    k_accept<<<lc.scan_blocks, 256, 0, st>>>(djob);
-    k_scan_reduce<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(djob);
-    k_scan_down<<<lc.scan_blocks, kScanThreads, 0, st>>>(djob);
+cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    const cudaError_t e = launch_count_lists(j, lc, st);
+    return e != cudaSuccess ? e : launch_count_tail(j, lc, st);
+}
+
+cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    k_scatter<<<lc.scan_blocks, 256, 0, st>>>(j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const Job* djob, const LaunchCfg& lc, cudaStream_t st) {
-    k_scatter<<<lc.scan_blocks, 256, 0, st>>>(djob);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg& lc, bool persistent,
+cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg& lc, bool persistent,
                               cudaStream_t st) {
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     const int wpb = lc.light_wpb;
     const size_t smem = light_smem_bytes(wpb);
-    if (persistent) {
-        k_light<true><<<lc.light_blocks, wpb * 32, smem, st>>>(djob, 1);
-    } else {
-        const int64_t nb = std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
-        k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(djob, 0);
-    }
-    k_medium<true><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(djob);
-    k_heavy<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(djob);
-    k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(djob);
+    Job j = job;
+    j.persistent = persistent ? 1 : 0;
+    const int64_t nb = persistent ? lc.light_blocks : std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
+    k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(j);
+    k_medium<true><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
+    k_heavy<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
     return cudaGetLastError();
 }
 
@@ -1411,9 +1394,9 @@ cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg
 // Allocation-free counting entry point (jpsi_select_noalloc, include/jpsi.h).
 //
 // For callers that may not allocate device memory at run time.  Its only
-// scratch is the file-scope array below: the job descriptor, the control
-// block, one class byte per event and the three per-event lists of the warp
-// kernel, for at most kNoAllocMaxEvents events.  Every GPU that loads the
+// scratch is the file-scope array below: the control block, one class byte
+// per event and the three per-event lists of the warp kernel, for at most
+// kNoAllocMaxEvents events (the job itself is a kernel parameter).  Every GPU that loads the
 // library holds the array until the process exits.  Host code must not use
 // the array's name as a device address: each device's address comes from
 // cudaGetSymbolAddress, taken once per device with that device current.
@@ -1421,12 +1404,10 @@ cudaError_t launch_emit_phase(const Job* djob, int64_t n_events, const LaunchCfg
 namespace jpsi {
 
 constexpr int64_t kNoAllocMaxEvents = (int64_t)1 << 18;  // 262,144 events per call
-constexpr size_t kNoAllocJobOff = 0;
-constexpr size_t kNoAllocCtrlOff = 512;
-constexpr size_t kNoAllocClassOff = 1024;
+constexpr size_t kNoAllocCtrlOff = 0;
+constexpr size_t kNoAllocClassOff = 512;
 constexpr size_t kNoAllocListOff = kNoAllocClassOff + (size_t)kNoAllocMaxEvents;
 constexpr size_t kNoAllocBytes = kNoAllocListOff + 3 * sizeof(int32_t) * (size_t)kNoAllocMaxEvents;
-static_assert(sizeof(Job) <= kNoAllocCtrlOff - kNoAllocJobOff, "job descriptor slot");
 static_assert(sizeof(Ctrl) <= kNoAllocClassOff - kNoAllocCtrlOff, "control block slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1469,7 +1450,6 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return JPSI_ECUDA;
     unsigned char* base = nullptr;
     if (noalloc_scratch(dev, &base) != cudaSuccess) return JPSI_ECUDA;
-    Job* djob = reinterpret_cast<Job*>(base + kNoAllocJobOff);
     Ctrl* dctrl = reinterpret_cast<Ctrl*>(base + kNoAllocCtrlOff);
     Job j{};
     j.x = b->x;
@@ -1493,6 +1473,7 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
         j.K = f;
     }
     j.grab = 2;
+    j.persistent = 1;
     j.unit_counts = unit_counts;
     j.track_counts = track_counts;
     j.ev_class = base + kNoAllocClassOff;
@@ -1508,9 +1489,8 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     const int wpb = 4;
     const int per_sm = light_max_blocks_per_sm(wpb);
     if (per_sm < 1) return JPSI_ECUDA;
-    if (cudaMemcpyAsync(djob, &j, sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess) return JPSI_ECUDA;
     if (cudaMemsetAsync(dctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return JPSI_ECUDA;  // counters start at zero
-    k_light<false><<<n_sm * per_sm, 32 * wpb, light_smem_bytes(wpb), st>>>(djob, 1);
+    k_light<false><<<n_sm * per_sm, 32 * wpb, light_smem_bytes(wpb), st>>>(j);
     if (cudaGetLastError() != cudaSuccess) return JPSI_ECUDA;
     Ctrl ctl{};
     if (cudaMemcpyAsync(&ctl, dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return JPSI_ECUDA;
