@@ -29,6 +29,10 @@ constexpr size_t kDefaultBudget = (size_t)8 << 30;
 constexpr int kMaxChunks = 8;            // jpsi_run_host pipelines copies and counting in up to 8 chunks
 constexpr int64_t kChunkMinEvents = 65536;
 
+// Trigger-slope pool of the block-tile path for a batch of `ne` events (an
+// event whose slopes find no room runs all its stations on one block).
+int64_t tpool_entries(int64_t ne) { return std::min<int64_t>(std::max<int64_t>(ne * 64, 1 << 16), 1 << 24); }
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -56,6 +60,7 @@ struct RunState {
     Ctrl* d_ctrl = nullptr;
     Ctrl* h_ctrl = nullptr;   // pinned
     DevBuf unit_counts, track_counts, ev_class, mlist, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
+    DevBuf tpool, tpool_alive, hT;
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
     Graph g_light, g_rest, g_emit, g_scatter;
     int g_cfg_id = -1;
@@ -231,6 +236,10 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     const size_t tl = (size_t)std::max(c->batch_cfg.heavy_blocks, c->plain_cfg.heavy_blocks) * kHeavyTCap;
     if ((st = ensure(c, rs.tlist, tl * sizeof(float2), "trigger lists")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.talive, tl, "trigger lists")) != JPSI_OK) return st;
+    const int64_t tp = tpool_entries(ne);
+    if ((st = ensure(c, rs.tpool, (size_t)tp * sizeof(float2), "trigger pool")) != JPSI_OK) return st;
+    if ((st = ensure(c, rs.tpool_alive, (size_t)tp, "trigger pool")) != JPSI_OK) return st;
+    if ((st = ensure(c, rs.hT, (size_t)std::max<int64_t>(ne, 1) * sizeof(int2), "event list")) != JPSI_OK) return st;
     const int64_t ntiles = (nu + 4095) / 4096 + 1;
     if ((st = ensure(c, rs.block_sums, (size_t)ntiles * 8, "scan")) != JPSI_OK) return st;
     if (!o->track_counts && (st = ensure(c, rs.track_counts, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts")))
@@ -263,6 +272,10 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.tlist = (float2*)rs.tlist.p;
     j.talive = (uint8_t*)rs.talive.p;
     j.tlist_cap = kHeavyTCap;
+    j.tpool = (float2*)rs.tpool.p;
+    j.tpool_alive = (uint8_t*)rs.tpool_alive.p;
+    j.tpool_cap = (int64_t)std::min(rs.tpool.bytes / sizeof(float2), rs.tpool_alive.bytes);
+    j.hT = (int2*)rs.hT.p;
     j.accept_bits = o->accept_bits;
     j.trip_off = o->trip_off ? o->trip_off : (int64_t*)rs.trip_off.p;
     j.block_sums = (int64_t*)rs.block_sums.p;
@@ -326,6 +339,9 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.glist);
     release(c, rs.tlist);
     release(c, rs.talive);
+    release(c, rs.tpool);
+    release(c, rs.tpool_alive);
+    release(c, rs.hT);
     release(c, rs.block_sums);
     release(c, rs.trip_off);
     release(c, rs.tscr);
@@ -897,6 +913,9 @@ jpsi_status jpsi_serve_start(jpsi_ctx* c, int n_slots, int64_t slot_events, int6
             (s = ensure(c, sl->rs.glist, (size_t)ne * 4, "slot list")) ||
             (s = ensure(c, sl->rs.tlist, (size_t)c->batch_cfg.heavy_blocks * kHeavyTCap * sizeof(float2), "slot trigger lists")) ||
             (s = ensure(c, sl->rs.talive, (size_t)c->batch_cfg.heavy_blocks * kHeavyTCap, "slot trigger lists")) ||
+            (s = ensure(c, sl->rs.tpool, (size_t)tpool_entries(ne) * sizeof(float2), "slot trigger pool")) ||
+            (s = ensure(c, sl->rs.tpool_alive, (size_t)tpool_entries(ne), "slot trigger pool")) ||
+            (s = ensure(c, sl->rs.hT, (size_t)ne * sizeof(int2), "slot list")) ||
             (s = ensure(c, sl->rs.block_sums, (size_t)((nu + 4095) / 4096 + 1) * 8, "slot scan")))
             break;
         // graphs are captured with the context's launch shape

@@ -36,7 +36,10 @@ struct Ctrl {
     int32_t n_medium;             // events sent to the medium warp kernel
     int32_t n_heavy;              // events sent to the block-tile kernel
     int32_t n_generic;            // events sent to the unpruned block kernel
-    unsigned long long work[8];   // persistent work counters: small, medium, heavy, generic (count); same (emit)
+    // persistent work counters: small, medium, heavy, generic (count); same
+    // (emit); [8] per-station units of the block-tile path (count)
+    unsigned long long work[10];
+    unsigned long long tpool_n;   // trigger slopes placed in the pool
     int64_t trip_total;           // copy of trip_off[n_units]
     unsigned long long scratch_n; // triplet entries appended by the counting pass
 };
@@ -65,6 +68,10 @@ struct Job {
     float2* tlist;                // [heavy blocks * tlist_cap] trigger slopes (block-tile kernel)
     uint8_t* talive;              // [heavy blocks * tlist_cap]
     int32_t tlist_cap;
+    float2* tpool;                // [tpool_cap] trigger slopes of block-tile events split by station
+    uint8_t* tpool_alive;         // [tpool_cap]
+    int64_t tpool_cap;
+    int2* hT;                     // [n_events] per block-tile list entry: pool start, slope count or state
     uint32_t* accept_bits;        // may be null
     int64_t* trip_off;            // [n_units + 1]
     int64_t* block_sums;          // scan scratch
@@ -86,16 +93,17 @@ struct LaunchCfg {
 
 // Launchers (jpsi_kernels.cu).  All asynchronous on `st`.
 // Count phase = small warp kernel, then the rest (medium warp kernel,
-// block-tile kernel, unpruned block kernel, accept bits, scan).  Kernel
-// launches per call: 1 and 7.
+// block-tile kernels, unpruned block kernel, accept bits, scan).  Kernel
+// launches per call: 1 and 9.
 cudaError_t launch_light_count(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st);
 cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 // The rest split in two, for counting a batch chunk by chunk: the medium,
-// block-tile and unpruned kernels (3 launches), then accept bits and scan (4).
+// block-tile (3 kernels) and unpruned kernels (5 launches), then accept
+// bits and scan (4).
 cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-constexpr int kLaunchesLight = 1, kLaunchesRest = 7, kLaunchesEmit = 4;
+constexpr int kLaunchesLight = 1, kLaunchesRest = 9, kLaunchesEmit = 4;
 // Places the counting pass's triplet entries at trip_off[unit] + rank.
 cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesScatter = 1;

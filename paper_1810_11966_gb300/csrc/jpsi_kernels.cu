@@ -108,7 +108,9 @@ struct HeavySmem {
     int32_t wsum[kHWarps];
     int red_i[kHWarps][2];
     float red_f[kHWarps][3];
-    int s_gi, s_rank, s_nT, s_cand;
+    unsigned long long s_pool;
+    long long s_item;
+    int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -851,93 +853,132 @@ __device__ int stage_station_block(const Job& j, HeavySmem& sm, int s) {
     return 0;
 }
 
-// One event on the block tile.  In the counting pass the event may move on
-// to the unpruned kernel (too large, extreme coordinates or too many
-// trigger triplets for the block's list).
+__device__ __forceinline__ void load_event_offsets(const Job& j, HeavySmem& sm, int64_t e) {
+    const int S3 = 3 * j.S;
+    for (int i = threadIdx.x; i <= S3; i += kHThreads) sm.off[i] = j.off[e * S3 + i];
+    __syncthreads();
+}
+
+// Job::hT[gi].y of a block-tile event: >= 0, its stations run on separate
+// blocks with that many trigger slopes in the pool from hT[gi].x on; or
+constexpr int kHTOwned = -1;  // its first block does (did) all of it
+constexpr int kHTMoved = -2;  // it went to the unpruned kernel
+
+// Hands an event from the block-tile path to the unpruned kernel, once (the
+// per-station blocks of one event may all find a reason).
+__device__ __forceinline__ void heavy_to_generic(const Job& j, int gi, int64_t e) {
+    if (atomicExch(&j.hT[gi].y, kHTMoved) != kHTMoved) push_event(j, e, kClsGeneric);
+}
+
+// One station of a block-tile event: staging, the triplet search of the
+// station (Sec. 3.2 steps 1-2) and, in CHAIN mode, the trigger slopes in
+// T[0, nT) that find no compatible triplet here lose their alive flag.
+// Counting pass: writes the unit count (also returned in cnt); returns false
+// when the event left the path (then nothing else may be done for it).
+// Emit pass: writes rows.  Block-uniform arguments; all threads call it.
 template <bool EMIT>
-__device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t e) {
+__device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, int64_t e, int s, TSink& ts,
+                           const float2* T, uint8_t* alive, int nT, int& cnt) {
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    const int S = j.S, S3 = 3 * S;
+    const int64_t u = e * j.S + s;
+    const int cnt_expected = EMIT ? j.unit_counts[u] : 0;
+    const int st = stage_station_block(j, sm, s);
+    if (st != 0) {
+        if (tid == 0) {
+            if (EMIT) {
+                atomicOr(&j.ctrl->status, kStEmitMismatch);
+            } else if (st == 1) {
+                atomicOr(&j.ctrl->status, kStInvalid);
+                j.ev_class[e] = kClsInvalid;
+            } else {
+                heavy_to_generic(j, gi, e);
+            }
+        }
+        return false;
+    }
+    if (tid == 0) sm.s_rank = 0;
+    __syncthreads();
+    int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
+    enum_station<EMIT, kNBH>(j, TileView<kNBH>{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
+                             cnt_expected, u, &sm.s_rank, kClsHeavy, wp, kHWarps);
+    __syncthreads();
+    cnt = sm.s_rank;
+    if (EMIT) {
+        if (tid == 0 && cnt != cnt_expected) atomicOr(&j.ctrl->status, kStEmitMismatch);
+        return true;
+    }
+    if (tid == 0) j.unit_counts[u] = cnt;
+    if (nT > 0) {
+        const TileView<kNBH> t{sm.P, sm.idx, sm.bst, sm.meta};
+        for (int ti = tid; ti < nT; ti += kHThreads)
+            if (alive[ti]) {
+                const float2 m = T[ti];
+                if (!road<kNBH>(j, t, c, m.x, m.y)) alive[ti] = 0;
+            }
+    }
+    return true;
+}
+
+// Counting pass of one block-tile event (list index gi).  The trigger
+// station comes first; in CHAIN mode its passing triplets' slopes go to the
+// block's own list, and then, when the trigger-slope pool has room, to the
+// pool: the other stations are then left to k_heavy_units (one block per
+// station) and k_heavy_final.  Otherwise this block does them itself.  The
+// event may move on to the unpruned kernel (too large, extreme coordinates
+// or too many trigger triplets for the block's list).
+__device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, int64_t e) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int S = j.S;
     const bool chain = j.mode == 1 && S > 1;
     const int nproc = j.mode == 1 ? S : 1;
-    for (int i = tid; i <= S3; i += kHThreads) sm.off[i] = j.off[e * S3 + i];
-    if (tid == 0) sm.s_nT = 0;
-    __syncthreads();
-    if (!EMIT) {
-        bool fits = true;
-        for (int si = 0; si < nproc; ++si) {
-            const int s = station_of(si, j.trig);
-            const int32_t* o = sm.off + 3 * s;
-            if (o[1] - o[0] > kHLayerCap || o[2] - o[1] > kHLayerCap || o[3] - o[2] > kHLayerCap ||
-                o[3] - o[0] > kHHCap)
-                fits = false;
-        }
-        if (!fits) {
-            if (tid == 0) push_event(j, e, kClsGeneric);
-            return;
-        }
+    if (tid == 0) {
+        sm.s_nT = 0;
+        j.hT[gi] = make_int2(0, kHTOwned);
     }
-    const TileView<kNBH> t{sm.P, sm.idx, sm.bst, sm.meta};
+    load_event_offsets(j, sm, e);
+    bool fits = true;
+    for (int si = 0; si < nproc; ++si) {
+        const int32_t* o = sm.off + 3 * station_of(si, j.trig);
+        if (o[1] - o[0] > kHLayerCap || o[2] - o[1] > kHLayerCap || o[3] - o[2] > kHLayerCap || o[3] - o[0] > kHHCap)
+            fits = false;
+    }
+    if (!fits) {
+        if (tid == 0) heavy_to_generic(j, gi, e);
+        return;
+    }
     float2* T = j.tlist + (int64_t)blockIdx.x * j.tlist_cap;
     uint8_t* alive = j.talive + (int64_t)blockIdx.x * j.tlist_cap;
     int trig_count = 0, nT = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
-        const int64_t u = e * S + s;
-        int cnt_expected = 0;
-        if (EMIT) {
-            cnt_expected = j.unit_counts[u];
-            if (cnt_expected == 0) continue;
-        }
-        const int st = stage_station_block(j, sm, s);
-        if (st != 0) {
-            if (tid == 0) {
-                if (EMIT) {
-                    atomicOr(&j.ctrl->status, kStEmitMismatch);
-                } else if (st == 1) {
-                    atomicOr(&j.ctrl->status, kStInvalid);
-                    j.ev_class[e] = kClsInvalid;
-                } else {
-                    push_event(j, e, kClsGeneric);
-                }
-            }
-            return;
-        }
-        if (tid == 0) sm.s_rank = 0;
-        __syncthreads();
-        const bool collect = !EMIT && chain && s == j.trig;
-        TSink ts{collect, T, j.tlist_cap, &sm.s_nT, 0};
-        int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
-        enum_station<EMIT, kNBH>(j, t, sm.queue[wp], lane, c, ts, rows, cnt_expected, u, &sm.s_rank, kClsHeavy, wp,
-                                 kHWarps);
-        __syncthreads();
-        const int cnt = sm.s_rank;
-        if (EMIT) {
-            if (tid == 0 && cnt != cnt_expected) atomicOr(&j.ctrl->status, kStEmitMismatch);
+        TSink ts{chain && si == 0, T, j.tlist_cap, &sm.s_nT, 0};
+        int cnt = 0;
+        if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) return;
+        if (si > 0) {
             __syncthreads();
             continue;
         }
-        if (tid == 0) j.unit_counts[u] = cnt;
-        if (s == j.trig) trig_count = cnt;
-        if (collect) {
-            nT = sm.s_nT;
-            if (nT > j.tlist_cap) {
-                if (tid == 0) push_event(j, e, kClsGeneric);
-                return;
+        trig_count = cnt;
+        if (!chain) break;
+        nT = sm.s_nT;
+        if (nT > j.tlist_cap) {
+            if (tid == 0) heavy_to_generic(j, gi, e);
+            return;
+        }
+        if (tid == 0) sm.s_pool = nT > 0 ? atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nT) : 0ull;
+        __syncthreads();
+        const unsigned long long pb = sm.s_pool;
+        if (pb + (unsigned long long)nT <= (unsigned long long)j.tpool_cap) {
+            for (int i = tid; i < nT; i += kHThreads) {
+                j.tpool[pb + i] = T[i];
+                j.tpool_alive[pb + i] = 1;
             }
-            for (int i = tid; i < nT; i += kHThreads) alive[i] = 1;
-            __syncthreads();
+            if (tid == 0) j.hT[gi] = make_int2((int)pb, nT);
+            return;
         }
-        if (chain && s != j.trig && nT > 0) {
-            for (int ti = tid; ti < nT; ti += kHThreads)
-                if (alive[ti]) {
-                    const float2 m = T[ti];
-                    if (!road<kNBH>(j, t, c, m.x, m.y)) alive[ti] = 0;
-                }
-        }
+        for (int i = tid; i < nT; i += kHThreads) alive[i] = 1;
         __syncthreads();
     }
-    if (EMIT) return;
     int tc = trig_count;
     if (chain) {
         if (tid == 0) sm.s_cand = 0;
@@ -957,22 +998,92 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int64_t 
     }
 }
 
-template <bool EMIT>
+// Counting pass: persistent blocks take block-tile events from the list.
 __global__ void __launch_bounds__(kHThreads, 3) k_heavy(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
     const Cuts c{j.cx, j.cy, j.K};
     const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
     for (;;) {
-        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 6 : 2], 1ull);
+        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[2], 1ull);
         __syncthreads();
         const int gi = sm.s_gi;
         __syncthreads();
         if (gi >= n_heavy) break;
-        const int64_t e = j.hlist[gi];
-        if (EMIT && j.ev_class[e] != kClsHeavy) continue;
-        heavy_event<EMIT>(j, sm, c, e);
+        heavy_event(j, sm, c, gi, j.hlist[gi]);
         __syncthreads();
+    }
+}
+
+// One block per (event, station) unit of the block-tile path.  Counting pass
+// (CHAIN): the non-trigger stations of events whose trigger slopes went to
+// the pool.  Emit pass: every processed station with triplets.
+template <bool EMIT>
+__global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_constant__ Job j) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
+    const int S = j.S;
+    if (!EMIT && (j.mode != 1 || S < 2)) return;
+    const int per = EMIT ? (j.mode == 1 ? S : 1) : S - 1;  // units per event
+    const Cuts c{j.cx, j.cy, j.K};
+    const long long n_items = (long long)*(volatile int32_t*)&j.ctrl->n_heavy * per;
+    for (;;) {
+        // thread 0 takes an item and decides (the state it reads may change
+        // under other blocks; the block must act on one reading)
+        if (threadIdx.x == 0) {
+            long long k = (long long)atomicAdd(&j.ctrl->work[EMIT ? 6 : 8], 1ull);
+            int hx = 0, hy = 0;
+            if (k < n_items) {
+                const int gi = (int)(k / per);
+                const int64_t e = j.hlist[gi];
+                const int s = station_of((int)(k % per) + (EMIT ? 0 : 1), j.trig);
+                bool skip = j.ev_class[e] != kClsHeavy;
+                if (EMIT) {
+                    skip |= j.unit_counts[e * S + s] == 0;
+                } else {
+                    const int2 h = j.hT[gi];
+                    hx = h.x;
+                    hy = h.y;
+                    skip |= hy < 0;  // finished by its first block, or moved on
+                }
+                if (skip) k = -1;
+            }
+            sm.s_item = k;
+            sm.s_hx = hx;
+            sm.s_hy = hy;
+        }
+        __syncthreads();
+        const long long k = sm.s_item;
+        const int hx = sm.s_hx, hy = sm.s_hy;
+        __syncthreads();
+        if (k >= n_items) break;
+        if (k < 0) continue;
+        const int gi = (int)(k / per);
+        const int64_t e = j.hlist[gi];
+        const int s = station_of((int)(k % per) + (EMIT ? 0 : 1), j.trig);
+        load_event_offsets(j, sm, e);
+        TSink ts{false, nullptr, 0, nullptr, 0};
+        int cnt = 0;
+        heavy_unit<EMIT>(j, sm, c, gi, e, s, ts, j.tpool + hx, j.tpool_alive + hx, hy, cnt);
+        __syncthreads();
+    }
+}
+
+// CHAIN track counts of the events whose stations ran on separate blocks:
+// the trigger slopes still alive after every station (one warp per event).
+__global__ void k_heavy_final(const __grid_constant__ Job j) {
+    if (j.mode != 1 || j.S < 2) return;
+    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < n_heavy; gi += nw) {
+        const int2 h = j.hT[gi];
+        const int64_t e = j.hlist[gi];
+        if (h.y < 0 || j.ev_class[e] != kClsHeavy) continue;
+        int a = 0;
+        for (int t = lane; t < h.y; t += 32) a += j.tpool_alive[h.x + t];
+        a = __reduce_add_sync(kFull, a);
+        if (lane == 0) j.track_counts[e] = a;
     }
 }
 
@@ -1290,9 +1401,13 @@ static cudaError_t ensure_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_medium<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)medium_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
+        e = cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem_bytes());
+        e = cudaFuncSetAttribute(k_heavy_units<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)heavy_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_heavy_units<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)heavy_smem_bytes());
     if (e == cudaSuccess) g_attr_done = true;
     return e;
 }
@@ -1309,7 +1424,7 @@ int light_max_blocks_per_sm(int wpb) {
 int heavy_max_blocks_per_sm() {
     if (ensure_attrs() != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heavy<false>, kHThreads, heavy_smem_bytes()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heavy, kHThreads, heavy_smem_bytes()) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1349,7 +1464,9 @@ cudaError_t launch_light_count(const Job& job, int64_t n_events, const LaunchCfg
 
 cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
     k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
-    k_heavy<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_heavy<<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_heavy_units<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_heavy_final<<<lc.scan_blocks, 256, 0, st>>>(j);
     k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
     return cudaGetLastError();
 }
@@ -1383,7 +1500,7 @@ cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg&
     const int64_t nb = persistent ? lc.light_blocks : std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
     k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(j);
     k_medium<true><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
-    k_heavy<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
+    k_heavy_units<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
     return cudaGetLastError();
 }
