@@ -115,17 +115,35 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """DRAM bytes per event of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+def ncu_record(kernel, workload, key):
+    """A per-event figure (`key`) of `kernel` from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(kernel, {}).get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash() or key not in e:
         return None
-    return float(e["dram_bytes_per_event"])
+    return float(e[key])
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per event of `kernel` (ncu dram__bytes_read + write)."""
+    return ncu_record(kernel, workload, "dram_bytes_per_event")
+
+
+def issue_roofline(inst_per_event, n_events, kernel_ms, n_sm, sm_mhz):
+    """Issue-slot roofline of a kernel: warp instructions per second against
+    one instruction per cycle on each of the 4 schedulers of every SM at the
+    SM clock seen under load."""
+    peak = n_sm * 4 * sm_mhz * 1e6
+    out = {"unit": "warp-inst/s", "peak": peak, "peak_kind": f"{n_sm} SMs x 4 schedulers x {sm_mhz:.0f} MHz",
+           "inst_per_event": inst_per_event, "achieved": None, "frac": None}
+    if inst_per_event is not None:
+        out["achieved"] = inst_per_event * n_events / (kernel_ms / 1000.0)
+        out["frac"] = out["achieved"] / peak
+    return out
 
 
 def algorithmic_bytes(n_events, n_hits, S):
@@ -595,7 +613,10 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_light_count", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if tpe is None else tpe * n_ev,
-                     "algorithmic_bytes": alg},
+                     "algorithmic_bytes": alg,
+                     "issue": issue_roofline(ncu_record("k_light_count", w.name, "inst_per_event"), n_ev, light_ms,
+                                             torch.cuda.get_device_properties(dev).multi_processor_count,
+                                             clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)},
         "e2e": {"value": world * n_ev / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1000 * e2e_mean},
         "gpu_launches": int(tm_b.kernel_launches),

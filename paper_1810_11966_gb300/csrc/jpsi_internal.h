@@ -94,16 +94,16 @@ struct LaunchCfg {
 // Launchers (jpsi_kernels.cu).  All asynchronous on `st`.
 // Count phase = small warp kernel, then the rest (medium warp kernel,
 // block-tile kernels, unpruned block kernel, accept bits, scan).  Kernel
-// launches per call: 1 and 9.
+// launches per call: 1 and 10.
 cudaError_t launch_light_count(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                                cudaStream_t st);
 cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 // The rest split in two, for counting a batch chunk by chunk: the medium,
-// block-tile (3 kernels) and unpruned kernels (5 launches), then accept
-// bits and scan (4).
+// block-tile (sort + 3 kernels) and unpruned kernels (6 launches), then
+// accept bits and scan (4).
 cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-constexpr int kLaunchesLight = 1, kLaunchesRest = 9, kLaunchesEmit = 4;
+constexpr int kLaunchesLight = 1, kLaunchesRest = 10, kLaunchesEmit = 4;
 // Places the counting pass's triplet entries at trip_off[unit] + rank.
 cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesScatter = 1;

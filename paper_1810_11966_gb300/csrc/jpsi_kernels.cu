@@ -998,6 +998,46 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
     }
 }
 
+// Orders the block-tile list by decreasing event size (hits), so the
+// persistent blocks take the largest events first and the smaller ones fill
+// in behind them.  One block, bitonic sort in shared memory; lists longer
+// than kSortCap keep their order (they have enough events to balance).
+constexpr int kSortCap = 4096;
+__global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ Job j) {
+    __shared__ unsigned long long key[kSortCap];  // hits << 32 | event
+    const int n = *(volatile int32_t*)&j.ctrl->n_heavy;
+    if (n < 2 || n > kSortCap) return;
+    int m = 2;
+    while (m < n) m <<= 1;
+    const int64_t S3 = 3 * j.S;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        unsigned long long k = 0;  // padding sorts last
+        if (i < n) {
+            const int32_t e = j.hlist[i];
+            const int64_t hits = j.off[(e + 1) * S3] - j.off[e * S3];
+            k = ((unsigned long long)hits << 32) | (uint32_t)e;
+        }
+        key[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int p = i ^ stride;
+                if (p > i) {
+                    const unsigned long long a = key[i], b = key[p];
+                    const bool down = (i & size) == 0;  // this run ends up decreasing
+                    if (down ? a < b : a > b) {
+                        key[i] = b;
+                        key[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) j.hlist[i] = (int32_t)(uint32_t)key[i];
+}
+
 // Counting pass: persistent blocks take block-tile events from the list.
 __global__ void __launch_bounds__(kHThreads, 3) k_heavy(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1464,6 +1504,7 @@ cudaError_t launch_light_count(const Job& job, int64_t n_events, const LaunchCfg
 
 cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
     k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
+    k_sort_heavy<<<1, 1024, 0, st>>>(j);
     k_heavy<<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_heavy_units<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_heavy_final<<<lc.scan_blocks, 256, 0, st>>>(j);

@@ -52,3 +52,27 @@ def test_two_gloo_ranks_shard_events(tmp_path, oracle_mod, synth_mod):
     uc = np.concatenate([np.load(tmp_path / f"uc{r}.npy") for r in range(world)])
     whole = oracle_mod.run(oracle_mod.params(4, 1, t_xz=0.25), synth_mod.generate("poisson20_1k", 0, world * n))
     assert np.array_equal(tc, whole["track_counts"]) and np.array_equal(uc, whole["unit_counts"])
+
+
+def test_bench_roofline_helpers(monkeypatch, tmp_path):
+    """Host arithmetic of the bench's roofline fields."""
+    import json as _json
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    r = bench.issue_roofline(10.0, 100, 1.0, 152, 2000.0)
+    assert r["peak"] == 152 * 4 * 2000e6
+    assert r["achieved"] == 10.0 * 100 / 1e-3 and r["frac"] == r["achieved"] / r["peak"]
+    assert bench.issue_roofline(None, 100, 1.0, 152, 2000.0)["frac"] is None
+    # a record taken on other kernel sources is not used
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"k": {"w": {"dram_bytes_per_event": 5.0, "inst_per_event": 7.0, "source_hash": bench.kernel_source_hash()}}}
+    (prof / "ncu_traffic.json").write_text(_json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["k"]["w"]["source_hash"])
+    assert bench.ncu_traffic("k", "w") == 5.0 and bench.ncu_record("k", "w", "inst_per_event") == 7.0
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "other")
+    assert bench.ncu_traffic("k", "w") is None
+    # algorithmic bytes of the counting kernel: hits, offsets, counts, class byte
+    assert bench.algorithmic_bytes(2, 10, 4) == 12 * 10 + 4 * (2 * 12 + 1) + 4 * 2 * 4 + 4 * 2 + 2
