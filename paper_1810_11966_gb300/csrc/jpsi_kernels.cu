@@ -204,14 +204,14 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
                                 int lane, int& nlive) {
     constexpr int R = Cfg::RMAX, NB = Cfg::NB, BPL = NB / 32;  // bins per lane
     float sx[R], sy[R];
-    bool lv[R];
+    int key[R];  // bin << 16 | rank in the bin once binned; -1: not stored
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) w.hist[BPL * lane + q] = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        lv[r] = false;
+        key[r] = -1;
         sx[r] = sy[r] = 0.0f;
     }
     // fast path: lanes past the end re-read the layer's last hit (a real hit,
@@ -224,7 +224,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         const int hc = in ? h : n - 1;
         const HitFast p = hit_fast(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
         bad |= !p.ok;
-        lv[r] = in;
+        key[r] = in ? 0 : -1;
         sx[r] = p.sx;
         sy[r] = p.sy;
         lo = fminf(lo, p.sx);
@@ -246,10 +246,11 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
             const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
             zbad |= in & p.zbad;
             wild |= in & p.wild;
-            lv[r] = in & p.live & !p.wild;
-            lo = lv[r] ? fminf(lo, p.sx) : lo;
-            hi = lv[r] ? fmaxf(hi, p.sx) : hi;
-            bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
+            const bool live = in & p.live & !p.wild;
+            key[r] = live ? 0 : -1;
+            lo = live ? fminf(lo, p.sx) : lo;
+            hi = live ? fmaxf(hi, p.sx) : hi;
+            bmax = live ? fmaxf(bmax, p.b) : bmax;
         }
         if (__any_sync(kFull, zbad)) return 1;
         if (__any_sync(kFull, wild)) return 2;
@@ -263,18 +264,12 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         if (!(inv_w < INFINITY)) inv_w = 0.0f;
     }
     __syncwarp();
-    int bin[R], rank[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        bin[r] = 0;
-        rank[r] = 0;
-    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
-        if (lv[r]) {
-            bin[r] = slope_bin<NB>(sx[r], lo, inv_w);
-            rank[r] = (int)atomicAdd(&w.hist[bin[r]], 1u);
+        if (key[r] >= 0) {
+            const int bin = slope_bin<NB>(sx[r], lo, inv_w);
+            key[r] = (bin << 16) | (int)atomicAdd(&w.hist[bin], 1u);
         }
     }
     __syncwarp();
@@ -300,8 +295,8 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
-        if (lv[r]) {
-            const int pos = bst[bin[r]] + rank[r];
+        if (key[r] >= 0) {
+            const int pos = bst[key[r] >> 16] + (key[r] & 0xffff);
             w.P[pos] = make_float2(sx[r], sy[r]);
             w.idx[pos] = (uint16_t)(lane + 32 * r);
         }
@@ -341,13 +336,13 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
                                  int& nlive) {
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     float sx[kHRMax], sy[kHRMax];
-    bool lv[kHRMax];
+    int key[kHRMax];  // bin << 16 | rank in the bin once binned; -1: not stored
     float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
     sm.hist[tid] = 0;
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
-        lv[r] = false;
+        key[r] = -1;
         sx[r] = sy[r] = 0.0f;
     }
 #pragma unroll
@@ -359,12 +354,13 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
         zbad |= in & p.zbad;
         wild |= in & p.wild;
-        lv[r] = in & p.live & !p.wild;
+        const bool live = in & p.live & !p.wild;
+        key[r] = live ? 0 : -1;
         sx[r] = p.sx;
         sy[r] = p.sy;
-        lo = lv[r] ? fminf(lo, p.sx) : lo;
-        hi = lv[r] ? fmaxf(hi, p.sx) : hi;
-        bmax = lv[r] ? fmaxf(bmax, p.b) : bmax;
+        lo = live ? fminf(lo, p.sx) : lo;
+        hi = live ? fmaxf(hi, p.sx) : hi;
+        bmax = live ? fmaxf(bmax, p.b) : bmax;
     }
     lo = warp_min(lo);
     hi = warp_max(hi);
@@ -395,18 +391,12 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         inv_w = __fdiv_rn((float)kNBH, __fsub_rn(hi, lo));
         if (!(inv_w < INFINITY)) inv_w = 0.0f;
     }
-    int bin[kHRMax], rank[kHRMax];
-#pragma unroll
-    for (int r = 0; r < kHRMax; ++r) {
-        bin[r] = 0;
-        rank[r] = 0;
-    }
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         if (kHThreads * r >= n) break;
-        if (lv[r]) {
-            bin[r] = slope_bin<kNBH>(sx[r], lo, inv_w);
-            rank[r] = (int)atomicAdd(&sm.hist[bin[r]], 1u);
+        if (key[r] >= 0) {
+            const int bin = slope_bin<kNBH>(sx[r], lo, inv_w);
+            key[r] = (bin << 16) | (int)atomicAdd(&sm.hist[bin], 1u);
         }
     }
     __syncthreads();
@@ -428,8 +418,8 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         if (kHThreads * r >= n) break;
-        if (lv[r]) {
-            const int pos = bst[bin[r]] + rank[r];
+        if (key[r] >= 0) {
+            const int pos = bst[key[r] >> 16] + (key[r] & 0xffff);
             sm.P[pos] = make_float2(sx[r], sy[r]);
             sm.idx[pos] = (uint16_t)(tid + kHThreads * r);
         }
