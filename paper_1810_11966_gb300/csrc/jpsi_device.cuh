@@ -154,6 +154,18 @@ __device__ __forceinline__ int slope_bin(float v, float lo, float inv_w) {
     return min(max(t, 0), NB - 1);
 }
 
+// Scale of a layer's bin map, about nb / (hi - lo) from the hardware
+// reciprocal: any finite scale >= 0 gives monotone bins, and queries use the
+// stored value, so it need not be rounded correctly.  0 when the range is
+// empty or the scale is not finite (every value then falls in bin 0).
+__device__ __forceinline__ float bin_scale(float lo, float hi, int nb) {
+    if (!(hi > lo)) return 0.0f;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fsub_rn(hi, lo)));
+    const float s = __fmul_rn((float)nb, r);
+    return s < INFINITY ? s : 0.0f;
+}
+
 // Bins that contain every stored value v with |v - c| <= W (1 + 2^-20):
 // the half-width is padded by 2^-18 W + 2^-20 |c|, which exceeds the rounding
 // of c -/+ W'' (<= eps (|c| + W'')).

@@ -45,19 +45,24 @@ namespace jpsi {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQCap = 128;                // pair queue entries per warp
 
-// warp path: tile shape per variant
+// warp path: tile shape per variant.  A layer's hits are sorted into
+// NY x NX cells: row = bin of s_y, column = bin of s_x (row-major), so the
+// cells of a slope window are one run of positions per row.  The small tile
+// uses one row (NY = 1): at about 100 hits per layer a second row saves
+// fewer candidate tests than its extra staging and window work costs.
 constexpr int kTCap = 64;                 // passing trigger triplets per event (CHAIN)
-template <int RMAX_, int HCAP_, int NB_, uint8_t CLS_, int WPB_>
+template <int RMAX_, int HCAP_, int NX_, int NY_, uint8_t CLS_, int WPB_>
 struct WCfg {
     static constexpr int RMAX = RMAX_;              // hits per lane per layer
     static constexpr int LAYER_CAP = 32 * RMAX_;    // hits per layer
     static constexpr int HCAP = HCAP_;              // hits per station tile
-    static constexpr int NB = NB_;                  // slope bins per layer
+    static constexpr int NX = NX_, NY = NY_;        // slope bins per layer in s_x, s_y
+    static constexpr int NC = NX_ * NY_;            // cells per layer
     static constexpr uint8_t CLS = CLS_;            // event class of this path
     static constexpr int WPB = WPB_;                // warps per block (medium: fixed)
 };
-using SmallCfg = WCfg<6, 384, 64, kClsLight, 0>;      // 192 hits/layer, 384/station
-using MediumCfg = WCfg<12, 960, 128, kClsMedium, 4>;  // 384 hits/layer, 960/station
+using SmallCfg = WCfg<6, 384, 64, 1, kClsLight, 0>;      // 192 hits/layer, 384/station
+using MediumCfg = WCfg<12, 960, 128, 2, kClsMedium, 4>;  // 384 hits/layer, 960/station
 
 // block-tile path
 constexpr int kHThreads = 256;
@@ -65,49 +70,56 @@ constexpr int kHWarps = kHThreads / 32;
 constexpr int kHRMax = 8;                         // hits per thread per layer
 constexpr int kHLayerCap = kHThreads * kHRMax;    // 2048 hits per layer
 constexpr int kHHCap = 6144;                      // hits per station tile
-constexpr int kNBH = 256;                         // slope bins per layer
+constexpr int kNXH = 128, kNYH = 4;               // slope bins per layer in s_x, s_y
+constexpr int kNCH = kNXH * kNYH;                 // cells per layer
 
 struct LayerMeta {
-    float lo, inv_w, bmax;  // bin map; bmax = largest pruning bound b of the layer
-    int32_t base;   // global index of the layer's first hit
-    int32_t pbase;  // tile position of the layer's first stored hit
-    int32_t nlive;  // stored hits (finite coordinates)
+    float lox, scx, loy, scy;  // cell map: column = bin of s_x, row = bin of s_y
+    float bmax;                // largest pruning bound b of the layer
+    int32_t base;              // global index of the layer's first hit
+    int32_t pbase;             // tile position of the layer's first stored hit
+    int32_t nlive;             // stored hits (finite coordinates)
 };
 
 // One station staged in shared memory: hit slopes (s_x, s_y) and layer-local
-// indices, sorted by layer then slope bin; bin starts and per-layer metadata.
-template <int NB>
+// indices, sorted by layer then cell; cell starts and per-layer metadata.
+template <int NX_, int NY_>
 struct TileView {
+    static constexpr int NX = NX_, NY = NY_, NC = NX_ * NY_;
     float2* P;
     uint16_t* idx;
-    uint16_t* bst;  // [3 * NB + 1] tile positions: layer l, bin b at l * NB + b
+    uint16_t* bst;  // [3 * NC + 1] tile positions: layer l, cell k at l * NC + k
     LayerMeta* meta;
-    __device__ __forceinline__ int bin_start(int l, int b) const { return bst[l * NB + b]; }
 };
+using HTile = TileView<kNXH, kNYH>;
 
 template <class Cfg>
 struct WarpTile {
     float2 P[Cfg::HCAP];
     uint16_t idx[Cfg::HCAP];
-    uint32_t queue[kQCap];
+    union {
+        uint32_t queue[kQCap];  // pair queue (enumeration)
+        uint32_t hist[Cfg::NC]; // cell counts of the layer being staged (staging)
+    };
     float2 T[kTCap];            // trigger triplet slopes
     uint8_t alive[kTCap];
-    uint16_t bst[3 * Cfg::NB + 1];
+    uint16_t bst[3 * Cfg::NC + 1];
     LayerMeta meta[3];
-    uint32_t hist[Cfg::NB];     // bin counts of the layer being staged
 };
 
 struct HeavySmem {
     float2 P[kHHCap];
     uint16_t idx[kHHCap];
-    uint32_t queue[kHWarps][kQCap];
-    uint16_t bst[3 * kNBH + 1];
+    union {
+        uint32_t queue[kHWarps][kQCap];
+        uint32_t hist[kNCH];
+    };
+    uint16_t bst[3 * kNCH + 1];
     LayerMeta meta[3];
-    uint32_t hist[kNBH];
     int32_t off[3 * kMaxStations + 1];
     int32_t wsum[kHWarps];
     int red_i[kHWarps][2];
-    float red_f[kHWarps][3];
+    float red_f[kHWarps][5];
     unsigned long long s_pool;
     long long s_item;
     int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy;
@@ -196,19 +208,20 @@ __device__ bool warp_load_offsets(const Job& j, int64_t e, int lane, EvOff& o) {
 // ------------------------------------------------------- warp staging
 
 // Stages one layer into the warp tile.  Returns 0, or 1 (z <= 0), or 2 (a
-// hit whose pruning bound is not finite).  Hits are counted into slope bins
-// with shared-memory atomics (the order inside a bin is not fixed; results
-// do not depend on it) and written sorted by bin.
+// hit whose pruning bound is not finite).  Hits are counted into cells with
+// shared-memory atomics (the order inside a cell is not fixed; results do
+// not depend on it) and written sorted by cell.
 template <class Cfg>
 __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t base, int32_t n, int32_t pbase,
                                 int lane, int& nlive) {
-    constexpr int R = Cfg::RMAX, NB = Cfg::NB, BPL = NB / 32;  // bins per lane
+    constexpr int R = Cfg::RMAX, NX = Cfg::NX, NY = Cfg::NY, NC = Cfg::NC, CPL = NC / 32;  // cells per lane
+    static_assert(NC % 32 == 0, "cells per layer");
     float sx[R], sy[R];
-    int key[R];  // bin << 16 | rank in the bin once binned; -1: not stored
-    float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
+    int key[R];  // cell << 16 | rank in the cell once binned; -1: not stored
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
     bool bad = false;
 #pragma unroll
-    for (int q = 0; q < BPL; ++q) w.hist[BPL * lane + q] = 0;
+    for (int q = 0; q < CPL; ++q) w.hist[CPL * lane + q] = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         key[r] = -1;
@@ -227,15 +240,17 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         key[r] = in ? 0 : -1;
         sx[r] = p.sx;
         sy[r] = p.sy;
-        lo = fminf(lo, p.sx);
-        hi = fmaxf(hi, p.sx);
+        lox = fminf(lox, p.sx);
+        hix = fmaxf(hix, p.sx);
+        loy = fminf(loy, p.sy);
+        hiy = fmaxf(hiy, p.sy);
         bmax = fmaxf(bmax, p.b);
     }
     if (__any_sync(kFull, bad)) {
         // some hit has an odd coordinate: classify every hit exactly
         bool zbad = false, wild = false;
-        lo = INFINITY;
-        hi = -INFINITY;
+        lox = loy = INFINITY;
+        hix = hiy = -INFINITY;
         bmax = 0.0f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -248,49 +263,53 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
             wild |= in & p.wild;
             const bool live = in & p.live & !p.wild;
             key[r] = live ? 0 : -1;
-            lo = live ? fminf(lo, p.sx) : lo;
-            hi = live ? fmaxf(hi, p.sx) : hi;
+            lox = live ? fminf(lox, p.sx) : lox;
+            hix = live ? fmaxf(hix, p.sx) : hix;
+            loy = live ? fminf(loy, p.sy) : loy;
+            hiy = live ? fmaxf(hiy, p.sy) : hiy;
             bmax = live ? fmaxf(bmax, p.b) : bmax;
         }
         if (__any_sync(kFull, zbad)) return 1;
         if (__any_sync(kFull, wild)) return 2;
     }
-    lo = warp_min(lo);
-    hi = warp_max(hi);
-    bmax = warp_max(bmax);
-    float inv_w = 0.0f;
-    if (hi > lo) {
-        inv_w = __fdiv_rn((float)NB, __fsub_rn(hi, lo));
-        if (!(inv_w < INFINITY)) inv_w = 0.0f;
+    lox = warp_min(lox);
+    hix = warp_max(hix);
+    if constexpr (NY > 1) {
+        loy = warp_min(loy);
+        hiy = warp_max(hiy);
     }
+    // the bounds are finite and > 0 here: their bit patterns order like the values
+    bmax = __int_as_float(__reduce_max_sync(kFull, __float_as_int(bmax)));
+    const float scx = bin_scale(lox, hix, NX), scy = NY > 1 ? bin_scale(loy, hiy, NY) : 0.0f;
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (32 * r >= n) break;
         if (key[r] >= 0) {
-            const int bin = slope_bin<NB>(sx[r], lo, inv_w);
-            key[r] = (bin << 16) | (int)atomicAdd(&w.hist[bin], 1u);
+            const int row = NY > 1 ? slope_bin<NY>(sy[r], loy, scy) : 0;
+            const int cell = row * NX + slope_bin<NX>(sx[r], lox, scx);
+            key[r] = (cell << 16) | (int)atomicAdd(&w.hist[cell], 1u);
         }
     }
     __syncwarp();
-    // exclusive scan of the NB bin counts, NB/32 consecutive bins per lane
-    int cs[BPL];
+    // exclusive scan of the NC cell counts, NC/32 consecutive cells per lane
+    int cs[CPL];
     int cnt = 0;
 #pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-        cs[q] = (int)w.hist[BPL * lane + q];
+    for (int q = 0; q < CPL; ++q) {
+        cs[q] = (int)w.hist[CPL * lane + q];
         cnt += cs[q];
     }
     const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    uint16_t* bst = w.bst + l * NB;  // the end of layer l is the start of layer l + 1
+    uint16_t* bst = w.bst + l * NC;  // the end of layer l is the start of layer l + 1
     int run = pbase + incl - cnt;
 #pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-        bst[BPL * lane + q] = (uint16_t)run;
+    for (int q = 0; q < CPL; ++q) {
+        bst[CPL * lane + q] = (uint16_t)run;
         run += cs[q];
     }
-    if (lane == 31) bst[NB] = (uint16_t)(pbase + total);
+    if (lane == 31) bst[NC] = (uint16_t)(pbase + total);
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -303,8 +322,10 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     }
     if (lane == 0) {
         LayerMeta m;
-        m.lo = lo;
-        m.inv_w = inv_w;
+        m.lox = lox;
+        m.scx = scx;
+        m.loy = loy;
+        m.scy = scy;
         m.bmax = bmax;
         m.base = base;
         m.pbase = pbase;
@@ -331,15 +352,19 @@ __device__ int stage_station_warp(const Job& j, WarpTile<Cfg>& w, int lane, cons
 
 // ------------------------------------------------------ block staging
 
-// Block version of the staging for the block-tile path (256 threads).
+// Block version of the staging for the block-tile path (256 threads, two
+// cells per thread).
 __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t base, int32_t n, int32_t pbase,
                                  int& nlive) {
+    constexpr int CPT = kNCH / kHThreads;  // cells per thread
+    static_assert(kNCH % kHThreads == 0, "cells per layer");
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     float sx[kHRMax], sy[kHRMax];
-    int key[kHRMax];  // bin << 16 | rank in the bin once binned; -1: not stored
-    float lo = INFINITY, hi = -INFINITY, bmax = 0.0f;
+    int key[kHRMax];  // cell << 16 | rank in the cell once binned; -1: not stored
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
-    sm.hist[tid] = 0;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) sm.hist[CPT * tid + q] = 0;
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         key[r] = -1;
@@ -358,18 +383,24 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         key[r] = live ? 0 : -1;
         sx[r] = p.sx;
         sy[r] = p.sy;
-        lo = live ? fminf(lo, p.sx) : lo;
-        hi = live ? fmaxf(hi, p.sx) : hi;
+        lox = live ? fminf(lox, p.sx) : lox;
+        hix = live ? fmaxf(hix, p.sx) : hix;
+        loy = live ? fminf(loy, p.sy) : loy;
+        hiy = live ? fmaxf(hiy, p.sy) : hiy;
         bmax = live ? fmaxf(bmax, p.b) : bmax;
     }
-    lo = warp_min(lo);
-    hi = warp_max(hi);
+    lox = warp_min(lox);
+    hix = warp_max(hix);
+    loy = warp_min(loy);
+    hiy = warp_max(hiy);
     bmax = warp_max(bmax);
     const int fz = __any_sync(kFull, zbad), fw = __any_sync(kFull, wild);
     if (lane == 0) {
-        sm.red_f[wp][0] = lo;
-        sm.red_f[wp][1] = hi;
-        sm.red_f[wp][2] = bmax;
+        sm.red_f[wp][0] = lox;
+        sm.red_f[wp][1] = hix;
+        sm.red_f[wp][2] = loy;
+        sm.red_f[wp][3] = hiy;
+        sm.red_f[wp][4] = bmax;
         sm.red_i[wp][0] = fz;
         sm.red_i[wp][1] = fw;
     }
@@ -377,31 +408,35 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     int anyz = 0, anyw = 0;
 #pragma unroll
     for (int q = 0; q < kHWarps; ++q) {
-        lo = fminf(lo, sm.red_f[q][0]);
-        hi = fmaxf(hi, sm.red_f[q][1]);
-        bmax = fmaxf(bmax, sm.red_f[q][2]);
+        lox = fminf(lox, sm.red_f[q][0]);
+        hix = fmaxf(hix, sm.red_f[q][1]);
+        loy = fminf(loy, sm.red_f[q][2]);
+        hiy = fmaxf(hiy, sm.red_f[q][3]);
+        bmax = fmaxf(bmax, sm.red_f[q][4]);
         anyz |= sm.red_i[q][0];
         anyw |= sm.red_i[q][1];
     }
     __syncthreads();
     if (anyz) return 1;
     if (anyw) return 2;
-    float inv_w = 0.0f;
-    if (hi > lo) {
-        inv_w = __fdiv_rn((float)kNBH, __fsub_rn(hi, lo));
-        if (!(inv_w < INFINITY)) inv_w = 0.0f;
-    }
+    const float scx = bin_scale(lox, hix, kNXH), scy = bin_scale(loy, hiy, kNYH);
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         if (kHThreads * r >= n) break;
         if (key[r] >= 0) {
-            const int bin = slope_bin<kNBH>(sx[r], lo, inv_w);
-            key[r] = (bin << 16) | (int)atomicAdd(&sm.hist[bin], 1u);
+            const int cell = slope_bin<kNYH>(sy[r], loy, scy) * kNXH + slope_bin<kNXH>(sx[r], lox, scx);
+            key[r] = (cell << 16) | (int)atomicAdd(&sm.hist[cell], 1u);
         }
     }
     __syncthreads();
-    // block exclusive scan of the 256 bin counts (one per thread)
-    const int cnt = (int)sm.hist[tid];
+    // block exclusive scan of the cell counts, CPT consecutive cells per thread
+    int cs[CPT];
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        cs[q] = (int)sm.hist[CPT * tid + q];
+        cnt += cs[q];
+    }
     const int incl = warp_incl_scan(cnt, lane);
     if (lane == 31) sm.wsum[wp] = incl;
     __syncthreads();
@@ -411,9 +446,14 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         woff += q < wp ? sm.wsum[q] : 0;
         total += sm.wsum[q];
     }
-    uint16_t* bst = sm.bst + l * kNBH;  // the end of layer l is the start of layer l + 1
-    bst[tid] = (uint16_t)(pbase + woff + incl - cnt);
-    if (tid == kHThreads - 1) bst[kNBH] = (uint16_t)(pbase + total);
+    uint16_t* bst = sm.bst + l * kNCH;  // the end of layer l is the start of layer l + 1
+    int run = pbase + woff + incl - cnt;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        bst[CPT * tid + q] = (uint16_t)run;
+        run += cs[q];
+    }
+    if (tid == kHThreads - 1) bst[kNCH] = (uint16_t)(pbase + total);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
@@ -426,8 +466,10 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     }
     if (tid == 0) {
         LayerMeta m;
-        m.lo = lo;
-        m.inv_w = inv_w;
+        m.lox = lox;
+        m.scx = scx;
+        m.loy = loy;
+        m.scy = scy;
         m.bmax = bmax;
         m.base = base;
         m.pbase = pbase;
@@ -439,12 +481,45 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     return 0;
 }
 
-template <int NB>
-__device__ __forceinline__ void layer_range(const TileView<NB>& t, int l, float c, float W, int& a, int& e) {
-    int b0, b1;
-    query_bins<NB>(c, W, t.meta[l].lo, t.meta[l].inv_w, b0, b1);
-    a = t.bin_start(l, b0);
-    e = t.bin_start(l, b1 + 1);
+// Cell window of a query: columns [x0, x1] around c_x +- W_x, rows [y0, y1]
+// around c_y +- W_y, each padded as in query_bins.  An intersection of
+// windows may be empty (x0 > x1 or y0 > y1).
+struct Win {
+    int x0, x1, y0, y1;
+};
+
+template <class TV>
+__device__ __forceinline__ Win cell_window(const TV& t, int l, float cx, float cy, float Wx, float Wy) {
+    const LayerMeta& m = t.meta[l];
+    Win w;
+    query_bins<TV::NX>(cx, Wx, m.lox, m.scx, w.x0, w.x1);
+    if constexpr (TV::NY > 1) {
+        query_bins<TV::NY>(cy, Wy, m.loy, m.scy, w.y0, w.y1);
+    } else {
+        w.y0 = w.y1 = 0;
+    }
+    return w;
+}
+
+__device__ __forceinline__ Win win_meet(const Win& a, const Win& b) {
+    return Win{max(a.x0, b.x0), min(a.x1, b.x1), max(a.y0, b.y0), min(a.y1, b.y1)};
+}
+
+// Tile positions of window w in layer l as two runs: its first row
+// [a, a + n0), and the positions from its second row's first column to its
+// last row's last column [a2, a2 + n1) (every cell in between included, a
+// superset when the window spans more than two rows; empty for one row).
+template <class TV>
+__device__ __forceinline__ void win_runs(const TV& t, int l, const Win& w, int& a, int& n0, int& a2, int& n1) {
+    a = n0 = a2 = n1 = 0;
+    if (w.x0 > w.x1 || w.y0 > w.y1) return;
+    const uint16_t* b = t.bst + l * TV::NC;
+    a = b[w.y0 * TV::NX + w.x0];
+    n0 = b[w.y0 * TV::NX + w.x1 + 1] - a;
+    if (w.y1 > w.y0) {
+        a2 = b[(w.y0 + 1) * TV::NX + w.x0];
+        n1 = b[w.y1 * TV::NX + w.x1 + 1] - a2;
+    }
 }
 
 // ---------------------------------------------------------- enumeration
@@ -459,38 +534,66 @@ struct TSink {
     int n;      // warp-local counter when sh_n is null
 };
 
-// Drains a pair queue: every (i, j) against the L2 hits of both bin windows.
-// The (pair, k) items of up to 32 pairs are spread evenly over the lanes (a
-// warp prefix sum over the window lengths; each lane finds the pair owning its
-// item by binary lifting).  Passing triplets get a rank inside their unit:
-// warp-local on the warp path, from a block-shared counter on the block path.
-template <bool EMIT, int NB>
-__device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
+// Items of up to 32 lanes laid end to end: lane i owns items [excl, excl +
+// n0 + n1), the first n0 at tile positions a.., the others at a2.. (runs of
+// win_runs).  An item's owner is found by owner_lane over excl.
+struct Runs {
+    int excl, total;    // this lane's first item; items of the warp
+    int sa, split, sb;  // item it of this lane sits at (it < split ? sa : sb) + it
+    bool two;           // some lane has a second run (warp-uniform)
+};
+
+template <int NY>
+__device__ __forceinline__ Runs runs_scan(int a, int n0, int a2, int n1, int lane) {
+    Runs r;
+    const int len = n0 + n1;
+    const int incl = warp_incl_scan(len, lane);
+    r.total = __shfl_sync(kFull, incl, 31);
+    r.excl = incl - len;
+    r.sa = a - r.excl;
+    r.split = r.excl + n0;
+    r.sb = a2 - r.split;
+    r.two = NY > 1 && __any_sync(kFull, n1 > 0);  // one-row tiles never have a second run
+    return r;
+}
+
+// Tile position of item `it`, owned by lane o (all lanes call it).
+template <int NY>
+__device__ __forceinline__ int runs_pos(const Runs& r, int o, int it) {
+    const int pa = __shfl_sync(kFull, r.sa, o) + it;
+    if (NY == 1 || !r.two) return pa;
+    const int sp = __shfl_sync(kFull, r.split, o), pb = __shfl_sync(kFull, r.sb, o) + it;
+    return it < sp ? pa : pb;
+}
+
+// Drains a pair queue: every (i, j) against the L2 hits in the meet of both
+// cell windows.  The (pair, k) items of up to 32 pairs are spread evenly over
+// the lanes (a warp prefix sum over the window sizes; each lane finds the
+// pair owning its item by binary lifting).  Passing triplets get a rank
+// inside their unit: warp-local on the warp path, from a block-shared counter
+// on the block path.
+template <bool EMIT, class TV>
+__device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
                       TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count) {
     const float B02 = __fadd_rn(t.meta[0].bmax, t.meta[2].bmax), B12 = __fadd_rn(t.meta[1].bmax, t.meta[2].bmax);
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int q = q0 + lane;
         uint32_t en = 0;
-        int kb = 0, len = 0;
+        int a = 0, m0 = 0, a2 = 0, m1 = 0;
         if (q < qn) {
             en = queue[q];
             const float2 Pi = t.P[en & 0xffffu], Pj = t.P[en >> 16];
-            int a1, e1, a2, e2;
-            layer_range<NB>(t, 2, Pi.x, B02, a1, e1);
-            layer_range<NB>(t, 2, Pj.x, B12, a2, e2);
-            kb = max(a1, a2);
-            len = max(min(e1, e2) - kb, 0);
+            const Win w = win_meet(cell_window(t, 2, Pi.x, Pi.y, B02, B02), cell_window(t, 2, Pj.x, Pj.y, B12, B12));
+            win_runs(t, 2, w, a, m0, a2, m1);
         }
-        const int incl = warp_incl_scan(len, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - len;
-        const int kshift = kb - excl;
+        const Runs rr = runs_scan<TV::NY>(a, m0, a2, m1, lane);
+        const int total = rr.total;
         for (int it0 = 0; it0 < total; it0 += 32) {
             const int it = it0 + lane;
-            const int o = owner_lane(excl, it);
+            const int o = owner_lane(rr.excl, it);
             const uint32_t eo = __shfl_sync(kFull, en, o);
-            const int ko = __shfl_sync(kFull, kshift, o) + it;
+            const int ko = runs_pos<TV::NY>(rr, o, it);
             bool ok = false;
             float mx = 0.f, my = 0.f;
             int ii = 0, jj = 0, kk = 0;
@@ -557,8 +660,8 @@ __device__ void drain(const Job& j, const TileView<NB>& t, const uint32_t* queue
 // hit's L1 candidate window (slope bins) spread over the lanes so every lane
 // tests one candidate pair per step; pairs that may belong to a passing
 // triplet are queued and drained against L2.
-template <bool EMIT, int NB>
-__device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue, int lane, const Cuts& c,
+template <bool EMIT, class TV>
+__device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane, const Cuts& c,
                             TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int warp,
                             int nwarps) {
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
@@ -569,17 +672,14 @@ __device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue
     for (int i0 = 32 * warp; i0 < n0; i0 += 32 * nwarps) {
         const bool has = i0 + lane < n0;
         const float2 Pi = t.P[p0 + (has ? i0 + lane : 0)];
-        int jb, je;
-        layer_range<NB>(t, 1, Pi.x, B01, jb, je);
-        const int len = has ? je - jb : 0;
-        const int incl = warp_incl_scan(len, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - len;
-        const int shift = jb - excl;  // candidate position = shift(owner) + item
+        int a = 0, m0 = 0, a2 = 0, m1 = 0;
+        if (has) win_runs(t, 1, cell_window(t, 1, Pi.x, Pi.y, B01, B01), a, m0, a2, m1);
+        const Runs rr = runs_scan<TV::NY>(a, m0, a2, m1, lane);
+        const int total = rr.total;
         for (int it0 = 0; it0 < total; it0 += 32) {
             const int it = it0 + lane;
-            const int o = owner_lane(excl, it);
-            const int pj = __shfl_sync(kFull, shift, o) + it;
+            const int o = owner_lane(rr.excl, it);
+            const int pj = runs_pos<TV::NY>(rr, o, it);
             const bool in = it < total;
             const float2 Po = t.P[p0 + i0 + o];
             const float2 Pj = t.P[in ? pj : p0];
@@ -590,25 +690,33 @@ __device__ int enum_station(const Job& j, const TileView<NB>& t, uint32_t* queue
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
-                    drain<EMIT, NB>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
+                    drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
                     qn = 0;
                 }
             }
         }
     }
     __syncwarp();
-    drain<EMIT, NB>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
+    drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
     return count;
 }
 
 // Does the staged station hold a passing triplet compatible with the
-// trigger slopes (mx, my)?  Per-thread search through the slope bins.
-template <int NB>
-__device__ bool road(const Job& j, const TileView<NB>& t, const Cuts& c, float mx, float my) {
+// trigger slopes (mx, my)?  Per-thread search through each layer's cells
+// inside the tube: one run of positions from the window's first cell to its
+// last (a superset when the window spans rows).
+template <class TV>
+__device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float my) {
     int a[3], e[3];
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-        layer_range<NB>(t, l, mx, __fadd_rn(t.meta[l].bmax, __fmul_rn(2.0f * kKappa, fabsf(mx))), a[l], e[l]);
+    for (int l = 0; l < 3; ++l) {
+        const float b = t.meta[l].bmax;
+        const Win w = cell_window(t, l, mx, my, __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx))),
+                                  __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my))));
+        const uint16_t* bs = t.bst + l * TV::NC;
+        a[l] = bs[w.y0 * TV::NX + w.x0];
+        e[l] = bs[w.y1 * TV::NX + w.x1 + 1];
+    }
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     const float b0 = t.meta[0].bmax, b1 = t.meta[1].bmax, b2 = t.meta[2].bmax;
     for (int p0 = a[0]; p0 < e[0]; ++p0) {
@@ -670,7 +778,7 @@ __device__ __forceinline__ bool fits_warp(const Job& j, const EvOff& o, int npro
 
 template <class Cfg>
 __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, const Cuts& c, int64_t e) {
-    constexpr int NB = Cfg::NB;
+    using TV = TileView<Cfg::NX, Cfg::NY>;
     constexpr bool kSmall = Cfg::CLS == kClsLight;
     EvOff o;
     const int S = j.S;
@@ -694,7 +802,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         const int s0 = j.mode == 1 ? 0 : j.trig, s1 = j.mode == 1 ? S : j.trig + 1;
         prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s1), lane);
     }
-    const TileView<NB> t{w.P, w.idx, w.bst, w.meta};
+    const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
@@ -712,7 +820,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
             return;
         }
         ts.on = chain && s == j.trig;
-        const int cnt = enum_station<false, NB>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
+        const int cnt = enum_station<false>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
                                                 0, 1);
         if (ts.on) {
             if (ts.n > kTCap) {
@@ -729,7 +837,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
             for (int ti = lane; ti < ts.n; ti += 32)
                 if (w.alive[ti]) {
                     const float2 m = w.T[ti];
-                    if (!road<NB>(j, t, c, m.x, m.y)) w.alive[ti] = 0;
+                    if (!road(j, t, c, m.x, m.y)) w.alive[ti] = 0;
                 }
             __syncwarp();
         }
@@ -749,7 +857,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
 
 template <class Cfg>
 __device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const Cuts& c, int64_t e) {
-    constexpr int NB = Cfg::NB;
+    using TV = TileView<Cfg::NX, Cfg::NY>;
     if (j.ev_class[e] != Cfg::CLS) return;
     const int S = j.S;
     const int nproc = j.mode == 1 ? S : 1;
@@ -758,7 +866,7 @@ __device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const
     if (!any) return;
     EvOff o;
     warp_load_offsets(j, e, lane, o);
-    const TileView<NB> t{w.P, w.idx, w.bst, w.meta};
+    const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, nullptr, 0, nullptr, 0};
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
@@ -769,7 +877,7 @@ __device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const
             if (lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
             return;
         }
-        const int got = enum_station<true, NB>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
+        const int got = enum_station<true>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
                                                nullptr, Cfg::CLS, 0, 1);
         if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
     }
@@ -785,8 +893,11 @@ __device__ __forceinline__ void light_event(const Job& j, WarpTile<Cfg>& w, int 
 
 // Small warp tiles: every event of the batch (statically one warp per event,
 // or persistent warps grabbing `grab` events at a time).
+// 56 registers: nine 4-warp blocks (36 warps) fit an SM by registers (the
+// 5.3 KB warp tiles would allow ten); measured faster than 64 registers with
+// eight blocks, despite some spills.
 template <bool EMIT>
-__global__ void __launch_bounds__(256, 4) k_light(const __grid_constant__ Job j) {
+__global__ void __maxnreg__(56) k_light(const __grid_constant__ Job j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     WarpTile<SmallCfg>& w = reinterpret_cast<WarpTile<SmallCfg>*>(smem_raw)[wi];
@@ -889,7 +1000,7 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
     if (tid == 0) sm.s_rank = 0;
     __syncthreads();
     int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
-    enum_station<EMIT, kNBH>(j, TileView<kNBH>{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
+    enum_station<EMIT>(j, HTile{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
                              cnt_expected, u, &sm.s_rank, kClsHeavy, wp, kHWarps);
     __syncthreads();
     cnt = sm.s_rank;
@@ -899,11 +1010,11 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
     }
     if (tid == 0) j.unit_counts[u] = cnt;
     if (nT > 0) {
-        const TileView<kNBH> t{sm.P, sm.idx, sm.bst, sm.meta};
+        const HTile t{sm.P, sm.idx, sm.bst, sm.meta};
         for (int ti = tid; ti < nT; ti += kHThreads)
             if (alive[ti]) {
                 const float2 m = T[ti];
-                if (!road<kNBH>(j, t, c, m.x, m.y)) alive[ti] = 0;
+                if (!road(j, t, c, m.x, m.y)) alive[ti] = 0;
             }
     }
     return true;
