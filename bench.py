@@ -459,7 +459,7 @@ def main():
     ap.add_argument("--workload", default="poisson100_1m")
     ap.add_argument("--events", type=int, default=None, help="events per rank (default: the workload's)")
     ap.add_argument("--mode", default="chain", choices=["chain", "paper"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-events", type=int, default=100_000)
     ap.add_argument("--ref-events", type=int, default=40_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -618,7 +618,9 @@ def main():
                                              torch.cuda.get_device_properties(dev).multi_processor_count,
                                              clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)},
         "e2e": {"value": world * n_ev / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1000 * e2e_mean},
+                "ms_per_step": 1000 * e2e_mean, "steps": len(e2e_t),
+                "ms_median": 1000 * sorted(e2e_t)[len(e2e_t) // 2], "ms_min": 1000 * min(e2e_t),
+                "ms_max": 1000 * max(e2e_t)},
         "gpu_launches": int(tm_b.kernel_launches),
         "clocks": clk,
         "triplets_per_step": cap,

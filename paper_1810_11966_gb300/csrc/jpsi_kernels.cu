@@ -798,15 +798,21 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         if (lane == 0) push_event(j, e, to_medium ? kClsMedium : kClsHeavy);
         return;
     }
-    {  // start every station's loads now: later stations stage from L2
-        const int s0 = j.mode == 1 ? 0 : j.trig, s1 = j.mode == 1 ? S : j.trig + 1;
-        prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s1), lane);
+    {  // the first station's lines start towards L2 now; each station then
+       // prefetches the next (prefetching all of them evicted some lines
+       // before use: 17 % more DRAM reads, against 4 % for one ahead)
+        const int s0 = station_of(0, j.trig);
+        prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s0 + 3), lane);
     }
     const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
+        if (si + 1 < nproc) {
+            const int sn = station_of(si + 1, j.trig);
+            prefetch_hits_l2(j, off_get(o, 3 * sn), off_get(o, 3 * sn + 3), lane);
+        }
         const int st = stage_station_warp<Cfg>(j, w, lane, o, s);
         if (st == 1) {
             if (lane == 0) {
