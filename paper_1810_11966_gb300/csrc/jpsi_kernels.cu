@@ -122,7 +122,7 @@ struct HeavySmem {
     float red_f[kHWarps][5];
     unsigned long long s_pool;
     long long s_item;
-    int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy;
+    int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy, s_next;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -656,20 +656,29 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
 }
 
 // All passing triplets of the staged station (Sec. 3.2 steps 1-2) found by
-// this warp: rounds of 32 L0 hits (rounds warp, warp + nwarps, ...), each
+// this warp: rounds of 32 L0 hits (all of them, or those this warp takes
+// from a block-shared counter when the warps of a block share a station), each
 // hit's L1 candidate window (slope bins) spread over the lanes so every lane
 // tests one candidate pair per step; pairs that may belong to a passing
 // triplet are queued and drained against L2.
-template <bool EMIT, class TV>
+template <bool EMIT, bool SHARED, class TV>
 __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane, const Cuts& c,
-                            TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int warp,
-                            int nwarps) {
+                            TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int* sh_next) {
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
     const int p0 = t.meta[0].pbase;
     const float B01 = __fadd_rn(t.meta[0].bmax, t.meta[1].bmax);
     int qn = 0, count = 0;
-    for (int i0 = 32 * warp; i0 < n0; i0 += 32 * nwarps) {
+    // rounds of 32 L0 hits: in order on the warp path; on the block path each
+    // warp takes the next one from a block-shared counter
+    auto next_round = [&]() {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(sh_next, 1);
+        return 32 * __shfl_sync(kFull, g, 0);
+    };
+    int i0 = 0;
+    if constexpr (SHARED) i0 = next_round();
+    for (; i0 < n0;) {
         const bool has = i0 + lane < n0;
         const float2 Pi = t.P[p0 + (has ? i0 + lane : 0)];
         int a = 0, m0 = 0, a2 = 0, m1 = 0;
@@ -695,6 +704,10 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
                 }
             }
         }
+        if constexpr (SHARED)
+            i0 = next_round();
+        else
+            i0 += 32;
     }
     __syncwarp();
     drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
@@ -826,8 +839,8 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
             return;
         }
         ts.on = chain && s == j.trig;
-        const int cnt = enum_station<false>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
-                                                0, 1);
+        const int cnt = enum_station<false, false>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
+                                            nullptr);
         if (ts.on) {
             if (ts.n > kTCap) {
                 if (lane == 0) push_event(j, e, kClsHeavy);
@@ -883,8 +896,8 @@ __device__ void light_event_emit(const Job& j, WarpTile<Cfg>& w, int lane, const
             if (lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
             return;
         }
-        const int got = enum_station<true>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
-                                               nullptr, Cfg::CLS, 0, 1);
+        const int got = enum_station<true, false>(j, t, w.queue, lane, c, ts, j.triplets + 3 * j.trip_off[u], cnt, u,
+                                           nullptr, Cfg::CLS, nullptr);
         if (got != cnt && lane == 0) atomicOr(&j.ctrl->status, kStEmitMismatch);
     }
 }
@@ -1003,11 +1016,14 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
         }
         return false;
     }
-    if (tid == 0) sm.s_rank = 0;
+    if (tid == 0) {
+        sm.s_rank = 0;
+        sm.s_next = 0;
+    }
     __syncthreads();
     int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
-    enum_station<EMIT>(j, HTile{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
-                             cnt_expected, u, &sm.s_rank, kClsHeavy, wp, kHWarps);
+    enum_station<EMIT, true>(j, HTile{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
+                       cnt_expected, u, &sm.s_rank, kClsHeavy, &sm.s_next);
     __syncthreads();
     cnt = sm.s_rank;
     if (EMIT) {
