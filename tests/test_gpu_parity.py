@@ -291,3 +291,51 @@ def test_run_host_pipelined_matches_device(lib, synth_mod):
     o.trip_capacity = dev["trip_needed"] - 1
     assert lib.jpsi_run_host(ctx.ctx, hb, o, 0) == lib.JPSI_ECAPACITY
     assert o.trip_needed == dev["trip_needed"] and np.array_equal(tc, dev["track_counts"])
+
+
+def _block_tile_events(rng, n_events, S, odd_hit=None):
+    """Events of about 500 hits in the middle layer of every station (past
+    the warp tiles), each with a few hits along one line from the target."""
+    zs = [130.0 + 35.0 * s + 10.0 * (li - 1) for s in range(S) for li in range(3)]
+    events = []
+    for k in range(n_events):
+        tx, ty = rng.uniform(-0.3, 0.3, 2)
+        ev = []
+        for q, z in enumerate(zs):
+            m = 500 if q % 3 == 1 else 60
+            r = rng.uniform(15, 0.4 * z, m)
+            ph = rng.uniform(0, 2 * np.pi, m)
+            hits = [(float(a * np.cos(p)), float(a * np.sin(p)), z) for a, p in zip(r, ph)]
+            hits += [(tx * z + rng.normal(0, 0.05), ty * z + rng.normal(0, 0.05), z) for _ in range(3)]
+            if odd_hit is not None and k % 3 == 0 and q == 2:  # station 0, a non-trigger station
+                hits.insert(int(rng.integers(len(hits))), odd_hit)
+            ev.append(hits)
+        events.append(ev)
+    return make_batch(events, S)
+
+
+def test_block_tile_station_blocks_hand_events_on(lib, oracle_mod):
+    # CHAIN on block-tile events: the stations other than the trigger run on
+    # their own blocks.  In every third event station 0 holds a finite hit
+    # whose slope overflows (x = 3e38 at z = 0.1), so the block of that
+    # station hands the event to the unpruned kernel; the rest stay split.
+    rng = np.random.default_rng(41)
+    b = _block_tile_events(rng, 12, 3, odd_hit=(3.0e38, 1.0, 0.1))
+    ref = _oracle(oracle_mod, 3, 1, 0.25, 0.25, b)
+    assert ref["track_counts"].max() > 0
+    ctx = _ctx(lib, 3, 1)
+    for form in ("plain", "batched"):
+        assert_same(gpu_select(ctx, b, form=form), ref, 36, label=form)
+    # the same events without the odd hit, in PAPER and CHAIN mode
+    b = _block_tile_events(np.random.default_rng(42), 12, 3)
+    for mode in (0, 1):
+        ref = _oracle(oracle_mod, 3, mode, 0.25, 0.25, b)
+        assert_same(gpu_select(_ctx(lib, 3, mode), b), ref, 36, label=f"mode={mode}")
+
+
+def test_block_tile_station_block_finds_invalid_z(lib, oracle_mod):
+    # z <= 0 in a non-trigger station of a block-tile event is found by that
+    # station's own block: the whole run reports JPSI_EINVAL
+    b = _block_tile_events(np.random.default_rng(43), 4, 3, odd_hit=(1.0, 1.0, -5.0))
+    r = gpu_select(_ctx(lib, 3, 1), b)
+    assert r["status"] == lib.JPSI_EINVAL
