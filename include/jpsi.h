@@ -166,11 +166,15 @@ jpsi_status jpsi_serve_stop(jpsi_ctx *ctx);
  * each run records CUDA events on its stream around its phases: the
  * warp-per-event counting kernel (light_ms), the rest of the counting phase
  * (block-per-event kernel, accept bits, scan: count_rest_ms) and the
- * triplet-writing phase (emit_ms).  Enabling resets the totals. */
+ * triplet-writing phase (emit_ms).  Enabling resets the totals.  The last
+ * two fields report the batched form's current launch shape (warps per
+ * block and events per grab of the warp-per-event kernel, as chosen by
+ * jpsi_autotune or the defaults 4 and 2). */
 typedef struct {
     int64_t runs;
     int64_t kernel_launches; /* kernels of this library launched by those runs */
     double light_ms, count_rest_ms, emit_ms;
+    int32_t light_wpb, light_grab;
 } jpsi_timing;
 jpsi_status jpsi_timing_enable(jpsi_ctx *ctx, int enable);
 jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);

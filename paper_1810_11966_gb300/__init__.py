@@ -48,7 +48,8 @@ class jpsi_outputs(ctypes.Structure):
 
 class jpsi_timing(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("light_ms", ctypes.c_double),
-                ("count_rest_ms", ctypes.c_double), ("emit_ms", ctypes.c_double)]
+                ("count_rest_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
+                ("light_wpb", ctypes.c_int32), ("light_grab", ctypes.c_int32)]
 
 
 _lib = None

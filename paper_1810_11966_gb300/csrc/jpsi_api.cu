@@ -796,6 +796,8 @@ jpsi_status jpsi_timing_get(jpsi_ctx* c, jpsi_timing* out) {
     if (!c || !out) return JPSI_EINVAL;
     std::lock_guard<std::mutex> lk(c->err_mu);
     *out = c->tm;
+    out->light_wpb = c->batch_cfg.light_wpb;
+    out->light_grab = c->grab;
     return JPSI_OK;
 }
 
