@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -109,9 +110,14 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code (comments and layout ignored), which
+    ties a committed ncu record to the kernels it was taken on."""
     h = hashlib.sha256()
     for f in ("jpsi_kernels.cu", "jpsi_device.cuh", "jpsi_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1810_11966_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1810_11966_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,23 +1,30 @@
 // Kernels of the J/psi first-level selection (arXiv:1810.11966, Sec. 3.2) on
-// sm_103a.  Work unit: one event (all of its stations).  Three paths, chosen
-// per event, give bit-identical results:
+// sm_103a.  Work unit: one event (on the block tile in CHAIN mode, one of its
+// stations).  Four paths, chosen per event, give bit-identical results:
 //
 //   k_light    one warp per event.  Each station's hits are staged from HBM
 //              (coalesced loads into registers) into a per-warp shared tile
-//              sorted into 64 slope bins per layer.  Pairs (L0, L1) whose
+//              sorted into cells (row = bin of s_y, column = bin of s_x; the
+//              small tile has one row of 64 columns).  Pairs (L0, L1) whose
 //              slopes are close enough to belong to a passing triplet are
 //              found with the candidate windows of 32 L0 hits spread evenly
 //              over the lanes, compacted into a pair queue with ballot/popc,
-//              and drained against the L2 hits of both bin windows; every
-//              surviving triple gets the exact FP32 fit (P1).  CHAIN mode
-//              keeps the passing trigger triplets' slopes in the tile and
-//              searches the other stations' tiles for compatible triplets
-//              (P2).  Limits: 192 hits per layer, 384 per station, 64
-//              passing trigger triplets.
-//   k_heavy    one 8-warp block per event for larger events: the same
-//              enumeration over a block tile (2048 hits per layer, 6144 per
-//              station, 256 slope bins), warps splitting the L0 rounds,
-//              trigger slopes in a per-block global list.
+//              and drained against the L2 hits in the meet of both windows;
+//              every surviving triple gets the exact FP32 fit (P1).  CHAIN
+//              mode keeps the passing trigger triplets' slopes in the tile
+//              and searches the other stations' tiles for compatible
+//              triplets (P2).  Limits: 192 hits per layer, 384 per station,
+//              64 passing trigger triplets.
+//   k_medium   the same code on a larger warp tile (384 hits per layer, 960
+//              per station, 2 x 128 cells) for the events k_light passes on.
+//   k_heavy, k_heavy_units, k_heavy_final
+//              8-warp blocks on a block tile (2048 hits per layer, 6144 per
+//              station, 4 x 128 cells), the warps taking L0 rounds from a
+//              shared counter.  k_sort_heavy orders these events largest
+//              first; k_heavy runs each one's trigger station and, in CHAIN
+//              mode, hands the other stations to k_heavy_units (one block
+//              per station, trigger slopes in a batch-wide pool) and
+//              k_heavy_final (alive slopes left per event).
 //   k_generic  one block per event, unpruned where the pruning bound is not
 //              finite (extreme coordinates) and no size limit: reads hits
 //              straight from global memory.
@@ -25,8 +32,9 @@
 //   k_scan*    exclusive scan of per-unit counts into int64 trip_off.
 //   k_scatter  moves the triplets recorded by the counting pass to their rows
 //              trip_off[unit] + rank; when the record overflowed, the emit
-//              variants of the three kernels re-enumerate instead.
+//              variants of the enumeration kernels re-enumerate instead.
 //
+// Every kernel takes the run's Job by value (a __grid_constant__ parameter).
 // Pruning only skips triples that provably fail P1 (see jpsi_device.cuh), and
 // P1/P2 are the same correctly rounded FP32 expressions everywhere.
 #include <cuda_runtime.h>
@@ -658,7 +666,7 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
 // All passing triplets of the staged station (Sec. 3.2 steps 1-2) found by
 // this warp: rounds of 32 L0 hits (all of them, or those this warp takes
 // from a block-shared counter when the warps of a block share a station), each
-// hit's L1 candidate window (slope bins) spread over the lanes so every lane
+// hit's L1 candidate window (its runs of cells) spread over the lanes so every lane
 // tests one candidate pair per step; pairs that may belong to a passing
 // triplet are queued and drained against L2.
 template <bool EMIT, bool SHARED, class TV>
