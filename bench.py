@@ -152,15 +152,23 @@ def issue_roofline(inst_per_event, n_events, kernel_ms, n_sm, sm_mhz):
     return out
 
 
-def algorithmic_bytes(n_events, n_hits, S):
-    """Bytes the counting kernel must move at least: every hit read once (12 B),
-    the CSR offsets (4 B each), per-unit counts (4 B), track count (4 B) and the
-    per-event class byte."""
-    return 12 * n_hits + 4 * (n_events * 3 * S + 1) + 4 * n_events * S + 4 * n_events + n_events
+def algorithmic_bytes(n_events, n_hits, S, offsets=None, trigger=None):
+    """Bytes the counting kernel must move at least: every processed hit read
+    once (12 B), the CSR offsets that locate them (4 B each), per-unit counts
+    (4 B), track count (4 B) and the per-event class byte.  CHAIN processes
+    every station; PAPER (trigger given, with the host offsets) only the
+    trigger station: its hits and its 4 offsets per event."""
+    out = 4 * n_events * S + 4 * n_events + n_events
+    if trigger is None:
+        return 12 * n_hits + 4 * (n_events * 3 * S + 1) + out
+    first = np.arange(n_events, dtype=np.int64) * 3 * S + 3 * trigger
+    hits = int((offsets[first + 3].astype(np.int64) - offsets[first]).sum())
+    return 12 * hits + 4 * 4 * n_events + out
 
 
-def cpu_baseline(workload, params_kw, n_events, threads=None):
-    """The oracle as it stands, on the host cores, over a bounded sample."""
+def cpu_baseline(workload, params_kw, n_events, n_single=None, threads=None):
+    """The oracle as it stands, on the host cores, over a bounded sample; and
+    on one thread over the first n_single events of it."""
     import oracle
     import synth
     threads = threads or (os.cpu_count() or 1)
@@ -170,9 +178,17 @@ def cpu_baseline(workload, params_kw, n_events, threads=None):
     r = oracle.run(p, b, triplets=True, n_threads=threads)
     dt = time.perf_counter() - t0
     assert r["status"] == 0
-    return {"value": n_events / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"events [0, {n_events}) of {workload}, counts + triplet lists, {threads} threads, "
-                      f"{dt:.2f} s wall"}
+    out = {"value": n_events / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"events [0, {n_events}) of {workload}, counts + triplet lists, {threads} threads, "
+                     f"{dt:.2f} s wall"}
+    if n_single:
+        b1 = synth.generate(workload, 0, n_single)
+        t0 = time.perf_counter()
+        r = oracle.run(p, b1, triplets=True, n_threads=1)
+        dt1 = time.perf_counter() - t0
+        assert r["status"] == 0
+        out["single_thread"] = {"value": n_single / dt1, "unit": UNIT, "events": n_single, "wall_s": round(dt1, 3)}
+    return out
 
 
 def reference_arm(args, rank, world):
@@ -283,6 +299,8 @@ def run_timeslices(args, w, dev, jp, torch):
             "slice_latency_ms": {"batched": percentiles(per_b, (50, 99)), "plain": percentiles(per_p, (50, 99))},
             "phases_ms": {"light_count": tm_b.light_ms, "count_rest": tm_b.count_rest_ms, "emit": tm_b.emit_ms},
             "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -399,6 +417,8 @@ def run_serving(args, w, dev, jp, torch):
                        "slots": args.slots, "slot_events": slot_events, "slot_hits": slot_hits,
                        "hbm_budget_gb": args.serve_budget_gb, "mode": args.mode},
             "saturation": sat, "loads": loads, "isolation_counts_equal": bool(same), "generate_s": gen_s}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -450,6 +470,8 @@ def run_stress(args, w, dev, jp, torch):
             "config": {"workload": w.name, "events": n_total, "chunk_events": chunk, "hits": hits,
                        "stations": w.n_stations, "window_cm": w.window, "mode": args.mode},
             "triplets": trips, "triplets_per_s": trips / (tot_ms / 1000), "generate_s": gen_s}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 32, n_single=4)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -607,7 +629,8 @@ def main():
     ms_p = tot_p / len(per_p)
     value = world * n_ev / (ms_b / 1000.0)
     light_ms = tm_b.light_ms / max(tm_b.runs, 1)
-    alg = algorithmic_bytes(n_ev, n_hits, S)
+    alg = (algorithmic_bytes(n_ev, n_hits, S) if args.mode == "chain" else
+           algorithmic_bytes(n_ev, n_hits, S, offsets=host["offsets"], trigger=p.trigger_station))
     peak, peak_kind = measured_peaks()
     achieved = alg / (light_ms / 1000.0) / 1e9
     tpe = ncu_traffic("k_light_count", w.name)
@@ -644,7 +667,8 @@ def main():
         "generate_s": gen_s,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), min(args.cpu_events, n_ev))
+        line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), min(args.cpu_events, n_ev),
+                                            n_single=min(10_000, n_ev))
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

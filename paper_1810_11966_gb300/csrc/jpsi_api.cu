@@ -224,7 +224,7 @@ jpsi_status check_batch(jpsi_ctx* c, const jpsi_batch* b, const jpsi_outputs* o,
 }
 
 // Prepares scratch and the job descriptor of a run.
-jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o) {
+jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, bool host_hits) {
     const int64_t S = c->p.n_stations;
     const int64_t ne = b->n_events, nu = ne * S;
     jpsi_status st;
@@ -263,6 +263,7 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.cy = c->cy;
     j.K = c->K;
     j.grab = c->grab;
+    j.host_hits = host_hits ? 1 : 0;
     j.unit_counts = (int32_t*)rs.unit_counts.p;
     j.track_counts = o->track_counts ? o->track_counts : (int32_t*)rs.track_counts.p;
     j.ev_class = (uint8_t*)rs.ev_class.p;
@@ -416,9 +417,9 @@ void add_timing(jpsi_ctx* c, RunState& rs, int launches, bool emitted) {
 
 // The common run: count phase, status/capacity check, emit phase.
 jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, cudaStream_t st,
-                       bool batched) {
+                       bool batched, bool host_hits = false) {
     jpsi_status s;
-    if ((s = prepare(c, rs, b, o)) != JPSI_OK) return s;
+    if ((s = prepare(c, rs, b, o, host_hits)) != JPSI_OK) return s;
     const int64_t ne = b->n_events, nu = ne * c->p.n_stations;
     cudaError_t e;
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
@@ -517,13 +518,41 @@ jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevB
     return JPSI_OK;
 }
 
-// jpsi_run on host buffers with the given device buffers.
+// Device addresses of a host batch whose arrays are all pinned (page-locked
+// and mapped into the device's address space); false when one is not.
+bool map_host_batch(const jpsi_batch* hb, jpsi_batch* db) {
+    *db = *hb;
+    const void* hp[4] = {hb->x, hb->y, hb->z, hb->offsets};
+    const void* dp[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) {
+        if (!hp[k]) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hp[k]) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+        dp[k] = a.devicePointer;
+    }
+    db->x = (const float*)dp[0];
+    db->y = (const float*)dp[1];
+    db->z = (const float*)dp[2];
+    db->offsets = (const int32_t*)dp[3];
+    return true;
+}
+
+// jpsi_run on host buffers with the given device buffers.  With `mapped`
+// (the batch's pinned arrays at their device addresses) the kernels read the
+// hits over the host link instead of from an uploaded copy.
 jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_outputs* ho, DevBuf& x, DevBuf& y,
                           DevBuf& z, DevBuf& off, DevBuf& acc, DevBuf& tc, DevBuf& toff, DevBuf& trip,
-                          int64_t trip_cap_dev, cudaStream_t st) {
+                          int64_t trip_cap_dev, cudaStream_t st, const jpsi_batch* mapped = nullptr) {
     jpsi_batch db;
-    jpsi_status s = upload(c, hb, x, y, z, off, &db, st);
-    if (s != JPSI_OK) return s;
+    jpsi_status s = JPSI_OK;
+    if (mapped)
+        db = *mapped;
+    else if ((s = upload(c, hb, x, y, z, off, &db, st)) != JPSI_OK)
+        return s;
     const int64_t ne = hb->n_events, nu = ne * c->p.n_stations;
     jpsi_outputs dout{};
     if (ho->accept_bits) {
@@ -544,7 +573,7 @@ jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_
         dout.triplets = (int32_t*)trip.p;
         dout.trip_capacity = cap;
     }
-    s = run_device(c, rs, &db, &dout, st, true);
+    s = run_device(c, rs, &db, &dout, st, true, mapped != nullptr);
     ho->trip_needed = dout.trip_needed;
     if (s != JPSI_OK && s != JPSI_ECAPACITY) return s;
     cudaError_t e = cudaSuccess;
@@ -610,7 +639,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         dout.triplets = (int32_t*)c->htrip.p;
         dout.trip_capacity = ho->trip_capacity;
     }
-    if ((s = prepare(c, rs, &db, &dout)) != JPSI_OK) return s;
+    if ((s = prepare(c, rs, &db, &dout, false)) != JPSI_OK) return s;
     const Job& all = rs.job;  // the whole batch (accept bits, scan, rows)
     cudaError_t e = cudaMemcpyAsync(c->hoff.p, hoff, obytes, cudaMemcpyHostToDevice, c->copy_stream);
     int k = 0;
@@ -778,6 +807,16 @@ jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, voi
     c->last_error.clear();
     jpsi_status s = check_batch(c, b, o, false);
     if (s != JPSI_OK) return s;
+    if (c->p.mode == JPSI_MODE_PAPER && c->p.n_stations > 1) {
+        // PAPER mode reads only the trigger station: from pinned buffers the
+        // kernels fetch just that station over the host link instead of
+        // copying every station first (the paper's host-side trigger
+        // filtering, Sec. 5.3, without a host-side gather)
+        jpsi_batch mb;
+        if (map_host_batch(b, &mb))
+            return run_host_with(c, c->rs, b, o, c->hx, c->hy, c->hz, c->hoff, c->hacc, c->htc, c->htoff, c->htrip,
+                                 -1, (cudaStream_t)stream, &mb);
+    }
     s = run_host_pipelined(c, c->rs, b, o, (cudaStream_t)stream);
     if (s != JPSI_EBUSY) return s;
     return run_host_with(c, c->rs, b, o, c->hx, c->hy, c->hz, c->hoff, c->hacc, c->htc, c->htoff, c->htrip, -1,

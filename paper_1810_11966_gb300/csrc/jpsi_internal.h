@@ -59,6 +59,7 @@ struct Job {
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
     int32_t persistent;           // warp kernels: persistent warps (1) or one warp per event (0)
+    int32_t host_hits;            // x, y, z, off are pinned host memory read over the link: no L2 prefetch
     int32_t* unit_counts;         // [n_events*S]
     int32_t* track_counts;        // [n_events]
     uint8_t* ev_class;            // [n_events]: kCls*

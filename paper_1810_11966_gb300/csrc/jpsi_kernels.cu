@@ -823,14 +823,14 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
        // prefetches the next (prefetching all of them evicted some lines
        // before use: 17 % more DRAM reads, against 4 % for one ahead)
         const int s0 = station_of(0, j.trig);
-        prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s0 + 3), lane);
+        if (!j.host_hits) prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s0 + 3), lane);
     }
     const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
-        if (si + 1 < nproc) {
+        if (si + 1 < nproc && !j.host_hits) {
             const int sn = station_of(si + 1, j.trig);
             prefetch_hits_l2(j, off_get(o, 3 * sn), off_get(o, 3 * sn + 3), lane);
         }

@@ -339,3 +339,31 @@ def test_block_tile_station_block_finds_invalid_z(lib, oracle_mod):
     b = _block_tile_events(np.random.default_rng(43), 4, 3, odd_hit=(1.0, 1.0, -5.0))
     r = gpu_select(_ctx(lib, 3, 1), b)
     assert r["status"] == lib.JPSI_EINVAL
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_run_host_pinned_matches_oracle(lib, oracle_mod, synth_mod, mode):
+    # pinned host buffers: PAPER mode reads the trigger station straight from
+    # host memory over the link (no upload), CHAIN mode copies every station;
+    # both equal the oracle, on log-normal events that reach every tile
+    import torch
+    n, S = 3000, 4
+    b = synth_mod.generate("lognormal_timeslices", 0, n)
+    assert np.diff(b["offsets"]).max() > 384  # some events run on the block tile
+    ref = _oracle(oracle_mod, S, mode, 0.25, 0.25, b)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("x", "y", "z", "offsets")}
+    acc = torch.zeros((n + 31) // 32, dtype=torch.int32).pin_memory()
+    tc = torch.zeros(n, dtype=torch.int32).pin_memory()
+    to = torch.zeros(n * S + 1, dtype=torch.int64).pin_memory()
+    tr = torch.zeros((ref["trip_needed"] + 3, 3), dtype=torch.int32).pin_memory()
+    o = lib.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off, o.triplets = acc.data_ptr(), tc.data_ptr(), to.data_ptr(), tr.data_ptr()
+    o.trip_capacity = tr.shape[0]
+    hb = lib.make_batch(pin["x"], pin["y"], pin["z"], pin["offsets"], n, b["n_hits"])
+    ctx = _ctx(lib, S, mode)
+    for _ in range(2):  # the second run reuses the context's buffers and graphs
+        s = lib.jpsi_run_host(ctx.ctx, hb, o, 0)
+        assert s == 0, lib.jpsi_strerror(s)
+        host = {"status": 0, "trip_needed": o.trip_needed, "accept_bits": acc.numpy().view(np.uint32),
+                "track_counts": tc.numpy(), "trip_off": to.numpy(), "triplets": tr.numpy()[: o.trip_needed]}
+        assert_same(host, ref, n * S, label=f"mode={mode}")

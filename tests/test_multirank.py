@@ -76,3 +76,7 @@ def test_bench_roofline_helpers(monkeypatch, tmp_path):
     assert bench.ncu_traffic("k", "w") is None
     # algorithmic bytes of the counting kernel: hits, offsets, counts, class byte
     assert bench.algorithmic_bytes(2, 10, 4) == 12 * 10 + 4 * (2 * 12 + 1) + 4 * 2 * 4 + 4 * 2 + 2
+    # PAPER mode: only the trigger station's hits (station 1: one hit in event 0, none in event 1)
+    # and its 4 offsets per event
+    off = np.array([0, 1, 1, 2, 3, 3, 3] + [3, 4, 4, 4, 4, 4], np.int32)  # 2 events x 2 stations x 3 layers
+    assert bench.algorithmic_bytes(2, 4, 2, offsets=off, trigger=1) == 12 * 1 + 4 * 4 * 2 + 4 * 2 * 2 + 4 * 2 + 2
