@@ -621,6 +621,20 @@ def main():
         ctx.check(jp.jpsi_run_host(ctx.ctx, hb, ho, st))
         e2e_t.append(time.perf_counter() - t0)
     e2e_mean = sum(e2e_t) / len(e2e_t)
+    # the same from a per-layer geometry table (z = NULL; the generator puts
+    # every hit on its layer's plane): 8 bytes per hit cross the host link
+    table = np.array([np.float32(zs + (l - 1) * w.layer_dz) for zs in w.station_z for l in range(3)], np.float32)
+    hbz = jp.make_batch(pin["x"], pin["y"], None, off_pin, n_ev, n_hits, z_layer=table)
+    h_tc2 = h_tc.clone()
+    for _ in range(3):
+        ctx.check(jp.jpsi_run_host(ctx.ctx, hbz, ho, st))
+    ez_t = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        ctx.check(jp.jpsi_run_host(ctx.ctx, hbz, ho, st))
+        ez_t.append(time.perf_counter() - t0)
+    assert np.array_equal(h_tc.numpy(), h_tc2.numpy())
+    ez_mean = sum(ez_t) / len(ez_t)
     h2d = 12 * n_hits + 4 * (n_ev * 3 * S + 1)
     d2h = 4 * ((n_ev + 31) // 32) + 4 * n_ev + 8 * (nu + 1) + 12 * cap
     assert np.array_equal(h_tc.numpy(), tc.cpu().numpy())
@@ -661,6 +675,11 @@ def main():
                 "ms_per_step": 1000 * e2e_mean, "steps": len(e2e_t),
                 "ms_median": 1000 * sorted(e2e_t)[len(e2e_t) // 2], "ms_min": 1000 * min(e2e_t),
                 "ms_max": 1000 * max(e2e_t), "ms_samples": [round(1000 * v, 2) for v in e2e_t]},
+        "e2e_layer_z": {"value": world * n_ev / ez_mean, "unit": UNIT,
+                        "h2d_bytes_per_step": 8 * n_hits + 4 * (n_ev * 3 * S + 1) + 4 * 3 * S,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * ez_mean,
+                        "ms_samples": [round(1000 * v, 2) for v in ez_t],
+                        "input": "x, y per hit + z per layer (jpsi_batch.z_layer); same results"},
         "gpu_launches": int(tm_b.kernel_launches),
         "clocks": clk,
         "triplets_per_step": cap,

@@ -35,6 +35,14 @@
  *             Layer 0 is the most upstream layer of its station.
  *   n_hits < 2^31; every z of a hit that the mode reads must not be <= 0
  *   (NaN and +Inf coordinates are legal and never pass).
+ *   z_layer   optional float32 [n_stations * 3], used when z is NULL: every
+ *             hit of layer l of station s lies at z = z_layer[s*3 + l] (the
+ *             detector layers are planes at fixed z, Sec. 2).  The library
+ *             fills a per-hit z array from it before the selection, so results
+ *             equal those of a per-hit z array holding the same values, and a
+ *             host run moves 8 instead of 12 bytes per hit.  It lives in the
+ *             same kind of memory as the call's other inputs.
+ *             jpsi_select_noalloc does not take it (z must be given).
  *
  * Outputs (device memory, caller-owned; any pointer may be NULL = not wanted,
  * except that triplets need trip_off):
@@ -96,8 +104,9 @@ typedef struct {
 typedef struct {
     int64_t n_events;
     int64_t n_hits;
-    const float *x, *y, *z;
+    const float *x, *y, *z; /* z may be NULL when z_layer is given */
     const int32_t *offsets;
+    const float *z_layer;   /* optional per-layer geometry, see above */
 } jpsi_batch;
 
 typedef struct {

@@ -38,7 +38,8 @@ class jpsi_params(ctypes.Structure):
 
 class jpsi_batch(ctypes.Structure):
     _fields_ = [("n_events", ctypes.c_int64), ("n_hits", ctypes.c_int64), ("x", ctypes.c_void_p),
-                ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
+                ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("z_layer", ctypes.c_void_p)]
 
 
 class jpsi_outputs(ctypes.Structure):
@@ -206,13 +207,16 @@ def _ptr(a):
     return a.ctypes.data if a.size else None
 
 
-def make_batch(x, y, z, offsets, n_events=None, n_hits=None) -> jpsi_batch:
-    """A jpsi_batch over torch tensors (device) or numpy arrays (host)."""
+def make_batch(x, y, z, offsets, n_events=None, n_hits=None, z_layer=None) -> jpsi_batch:
+    """A jpsi_batch over torch tensors (device) or numpy arrays (host).  z may
+    be None when z_layer (n_stations * 3 floats, same memory kind) is given."""
     b = jpsi_batch()
     nev = n_events if n_events is not None else (len(offsets) - 1) // 3
     b.n_events = int(nev)
     b.n_hits = int(n_hits if n_hits is not None else len(x))
-    b.x, b.y, b.z, b.offsets = _ptr(x), _ptr(y), _ptr(z), _ptr(offsets)
+    b.x, b.y, b.offsets = _ptr(x), _ptr(y), _ptr(offsets)
+    b.z = None if z is None else _ptr(z)
+    b.z_layer = None if z_layer is None else _ptr(z_layer)
     return b
 
 
@@ -243,13 +247,14 @@ class Context:
         if s != JPSI_OK:
             raise JpsiError(s, self.last_error())
 
-    def select(self, x, y, z, offsets, n_events, *, triplets=True, capacity=None, form="batched", stream=None):
+    def select(self, x, y, z, offsets, n_events, *, triplets=True, capacity=None, form="batched", stream=None,
+               z_layer=None):
         """Runs the selection on device tensors.  Returns a dict with the run's
         status and the device tensors accept_bits, track_counts, trip_off,
         triplets ([n,3]) and trip_needed (statuses are returned, not
         raised).  With capacity=None the call sizes the triplet buffer from a
         first counting run (two calls, like the library's own two-pass
-        contract)."""
+        contract).  z may be None with a per-layer table z_layer (device)."""
         import torch
         dev = torch.device("cuda", self.device)
         S = self.p.n_stations
@@ -259,7 +264,7 @@ class Context:
             "track_counts": torch.empty(max(n_events, 1), dtype=torch.int32, device=dev),
             "trip_off": torch.empty(nu + 1, dtype=torch.int64, device=dev),
         }
-        b = make_batch(x, y, z, offsets, n_events)
+        b = make_batch(x, y, z, offsets, n_events, z_layer=z_layer)
         o = jpsi_outputs()
         o.accept_bits = out["accept_bits"].data_ptr()
         o.track_counts = out["track_counts"].data_ptr()

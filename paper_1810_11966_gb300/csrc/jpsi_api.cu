@@ -61,6 +61,7 @@ struct RunState {
     Ctrl* h_ctrl = nullptr;   // pinned
     DevBuf unit_counts, track_counts, ev_class, mlist, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
     DevBuf tpool, tpool_alive, hT;
+    DevBuf zfill, ztab;  // per-hit z filled from a batch's z_layer table; the table on the device
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
     Graph g_light, g_rest, g_emit, g_scatter;
     int g_cfg_id = -1;
@@ -212,11 +213,12 @@ jpsi_status check_batch(jpsi_ctx* c, const jpsi_batch* b, const jpsi_outputs* o,
     if (b->n_events > (((int64_t)1 << 31) - 2) / (3 * S)) return fail(c, JPSI_EINVAL, "too many events for int32 offsets");
     if (b->n_events == 0 && b->n_hits != 0) return fail(c, JPSI_EINVAL, "hits without events");
     if (b->n_events > 0 && !b->offsets) return fail(c, JPSI_EINVAL, "offsets missing");
-    if (b->n_hits > 0 && (!b->x || !b->y || !b->z)) return fail(c, JPSI_EINVAL, "hit arrays missing");
+    if (b->n_hits > 0 && (!b->x || !b->y || (!b->z && !b->z_layer))) return fail(c, JPSI_EINVAL, "hit arrays missing");
     if (o->triplets && !o->trip_off) return fail(c, JPSI_EINVAL, "triplets need trip_off");
     if (o->trip_capacity < 0) return fail(c, JPSI_EINVAL, "negative triplet capacity");
     if (device_ptrs) {
-        const void* ptrs[] = {b->x, b->y, b->z, b->offsets, o->accept_bits, o->track_counts, o->trip_off, o->triplets};
+        const void* ptrs[] = {b->x, b->y, b->z, b->offsets, b->z_layer, o->accept_bits, o->track_counts, o->trip_off,
+                              o->triplets};
         for (const void* p : ptrs)
             if (!device_accessible(c, p)) return fail(c, JPSI_EINVAL, "pointer is not device-accessible");
     }
@@ -343,6 +345,8 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.tpool);
     release(c, rs.tpool_alive);
     release(c, rs.hT);
+    release(c, rs.zfill);
+    release(c, rs.ztab);
     release(c, rs.block_sums);
     release(c, rs.trip_off);
     release(c, rs.tscr);
@@ -419,6 +423,17 @@ void add_timing(jpsi_ctx* c, RunState& rs, int launches, bool emitted) {
 jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, cudaStream_t st,
                        bool batched, bool host_hits = false) {
     jpsi_status s;
+    jpsi_batch bz;
+    if (!b->z && b->n_hits > 0) {
+        // per-hit z from the batch's geometry table (device memory)
+        if ((s = ensure(c, rs.zfill, (size_t)b->n_hits * 4, "hits z")) != JPSI_OK) return s;
+        const cudaError_t e = launch_expand_z(b->offsets, b->z_layer, (float*)rs.zfill.p, 0, b->n_events,
+                                              c->p.n_stations, b->n_hits, c->n_sm, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "z from geometry");
+        bz = *b;
+        bz.z = (const float*)rs.zfill.p;
+        b = &bz;
+    }
     if ((s = prepare(c, rs, b, o, host_hits)) != JPSI_OK) return s;
     const int64_t ne = b->n_events, nu = ne * c->p.n_stations;
     cudaError_t e;
@@ -493,7 +508,7 @@ void set_launch_shape(jpsi_ctx* c, int wpb, int grab) {
 }
 
 // Copies H2D of a host batch into device buffers `x, y, z, off`.
-jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevBuf& z, DevBuf& off,
+jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevBuf& z, DevBuf& off, DevBuf& ztab,
                    jpsi_batch* db, cudaStream_t st) {
     const int64_t S = c->p.n_stations;
     const size_t hb_bytes = (size_t)hb->n_hits * 4;
@@ -506,9 +521,17 @@ jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevB
     if (hb_bytes) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(x.p, hb->x, hb_bytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(y.p, hb->y, hb_bytes, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(z.p, hb->z, hb_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && hb->z) e = cudaMemcpyAsync(z.p, hb->z, hb_bytes, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && hb->n_events > 0) e = cudaMemcpyAsync(off.p, hb->offsets, ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !hb->z && hb_bytes) {
+        // per-hit z filled on the device from the geometry table
+        if ((s = ensure(c, ztab, (size_t)S * 3 * 4, "z table")) != JPSI_OK) return s;
+        e = cudaMemcpyAsync(ztab.p, hb->z_layer, (size_t)S * 3 * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = launch_expand_z((const int32_t*)off.p, (const float*)ztab.p, (float*)z.p, 0, hb->n_events, (int)S,
+                                hb->n_hits, c->n_sm, st);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "input upload");
     *db = *hb;
     db->x = (const float*)x.p;
@@ -522,6 +545,7 @@ jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevB
 // and mapped into the device's address space); false when one is not.
 bool map_host_batch(const jpsi_batch* hb, jpsi_batch* db) {
     *db = *hb;
+    if (hb->n_hits > 0 && !hb->z) return false;  // z from a table: uploaded and filled instead
     const void* hp[4] = {hb->x, hb->y, hb->z, hb->offsets};
     const void* dp[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k) {
@@ -551,7 +575,7 @@ jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_
     jpsi_status s = JPSI_OK;
     if (mapped)
         db = *mapped;
-    else if ((s = upload(c, hb, x, y, z, off, &db, st)) != JPSI_OK)
+    else if ((s = upload(c, hb, x, y, z, off, rs.ztab, &db, st)) != JPSI_OK)
         return s;
     const int64_t ne = hb->n_events, nu = ne * c->p.n_stations;
     jpsi_outputs dout{};
@@ -641,7 +665,11 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
     }
     if ((s = prepare(c, rs, &db, &dout, false)) != JPSI_OK) return s;
     const Job& all = rs.job;  // the whole batch (accept bits, scan, rows)
+    const bool ztable = !hb->z;  // z filled per chunk from the geometry table
+    if (ztable && (s = ensure(c, rs.ztab, (size_t)S * 3 * 4, "z table")) != JPSI_OK) return s;
     cudaError_t e = cudaMemcpyAsync(c->hoff.p, hoff, obytes, cudaMemcpyHostToDevice, c->copy_stream);
+    if (e == cudaSuccess && ztable)
+        e = cudaMemcpyAsync(rs.ztab.p, hb->z_layer, (size_t)S * 3 * 4, cudaMemcpyHostToDevice, c->copy_stream);
     int k = 0;
     for (int64_t e0 = 0; e0 < ne && e == cudaSuccess; e0 += cs, ++k) {
         const int64_t e1 = std::min(ne, e0 + cs);
@@ -650,7 +678,8 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         if (nb) {
             e = cudaMemcpyAsync((float*)c->hx.p + h0, hb->x + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync((float*)c->hy.p + h0, hb->y + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync((float*)c->hz.p + h0, hb->z + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
+            if (e == cudaSuccess && !ztable)
+                e = cudaMemcpyAsync((float*)c->hz.p + h0, hb->z + h0, nb, cudaMemcpyHostToDevice, c->copy_stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(rs.chunk_ev[k], c->copy_stream);
     }
@@ -664,6 +693,8 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         jk.ev_begin = e0;
         jk.ev_count = e1 - e0;
         if ((e = cudaStreamWaitEvent(st, rs.chunk_ev[k], 0)) != cudaSuccess ||
+            (ztable && (e = launch_expand_z((const int32_t*)c->hoff.p, (const float*)rs.ztab.p, (float*)c->hz.p, e0,
+                                            e1, (int)S, hb->n_hits, c->n_sm, st)) != cudaSuccess) ||
             (k > 0 && (e = cudaMemsetAsync((char*)rs.d_ctrl + ctr_off, 0, ctr_len, st)) != cudaSuccess) ||
             (e = launch_light_count(jk, e1 - e0, c->batch_cfg, true, st)) != cudaSuccess ||
             (e = launch_count_lists(jk, c->batch_cfg, st)) != cudaSuccess)

@@ -112,6 +112,10 @@ constexpr int kLaunchesScatter = 1;
 // re-enumerate their units and write rows at trip_off.
 cudaError_t launch_emit_phase(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                               cudaStream_t st);
+// Per-hit z of events [ev0, ev1) from a per-layer table z_layer[S*3] (device
+// pointers; one launch).
+cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, int64_t ev0, int64_t ev1, int S,
+                            int64_t n_hits, int n_sm, cudaStream_t st);
 size_t light_smem_bytes(int wpb);
 int light_max_blocks_per_sm(int wpb);
 int generic_max_blocks_per_sm(int threads);

@@ -1551,6 +1551,33 @@ __global__ void k_scatter(const __grid_constant__ Job j) {
     }
 }
 
+// ------------------------------------------------- per-layer z geometry
+
+// Per-hit z from a detector geometry table (every hit of layer l of station s
+// at z_layer[s*3 + l]) for events [ev0, ev1): blocks take events in turn;
+// each hit finds its layer among the event's 3S+1 offsets by binary search.
+// Writes stay inside [0, n_hits) whatever the offsets hold (malformed offsets
+// fail the selection afterwards), and the table index stays below 3S.
+__global__ void __launch_bounds__(256) k_expand_z(const int32_t* __restrict__ off,
+                                                  const float* __restrict__ z_layer, float* __restrict__ z,
+                                                  int64_t ev0, int64_t ev1, int S, int64_t n_hits) {
+    __shared__ int32_t so[3 * kMaxStations + 1];
+    const int S3 = 3 * S;
+    for (int64_t e = ev0 + blockIdx.x; e < ev1; e += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i <= S3; i += blockDim.x) so[i] = off[e * S3 + i];
+        __syncthreads();
+        const int64_t h0 = max((int64_t)so[0], (int64_t)0), h1 = min((int64_t)so[S3], n_hits);
+        for (int64_t h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
+            int q = 0;  // last layer q < S3 with so[q] <= h
+#pragma unroll
+            for (int step = 32; step > 0; step >>= 1)
+                if (q + step < S3 && so[q + step] <= h) q += step;
+            z[h] = z_layer[q];
+        }
+    }
+}
+
 // ------------------------------------------------------------ launchers
 
 size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile<SmallCfg>); }
@@ -1654,6 +1681,14 @@ cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st
 cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
     const cudaError_t e = launch_count_lists(j, lc, st);
     return e != cudaSuccess ? e : launch_count_tail(j, lc, st);
+}
+
+cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, int64_t ev0, int64_t ev1, int S,
+                            int64_t n_hits, int n_sm, cudaStream_t st) {
+    if (ev1 <= ev0) return cudaSuccess;
+    const int64_t grid = std::min<int64_t>(ev1 - ev0, (int64_t)n_sm * 8);
+    k_expand_z<<<(unsigned)grid, 256, 0, st>>>(off, z_layer, z, ev0, ev1, S, n_hits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st) {

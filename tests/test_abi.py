@@ -35,11 +35,29 @@ def test_strerror_without_gpu():
     assert lib.jpsi_strerror(3) == b"triplet buffer too small"
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    # the binding's ctypes structs against the C header, field by field: a C
+    # program built with gcc from include/jpsi.h prints sizes and offsets
+    import subprocess
     import paper_1810_11966_gb300 as jp
-    assert ctypes.sizeof(jp.jpsi_params) == 28
-    assert ctypes.sizeof(jp.jpsi_batch) == 48
-    assert ctypes.sizeof(jp.jpsi_outputs) == 48
+    structs = {"jpsi_params": jp.jpsi_params, "jpsi_batch": jp.jpsi_batch, "jpsi_outputs": jp.jpsi_outputs,
+               "jpsi_timing": jp.jpsi_timing}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "jpsi.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
 
 
 def test_built_for_sm103a():

@@ -367,3 +367,67 @@ def test_run_host_pinned_matches_oracle(lib, oracle_mod, synth_mod, mode):
         host = {"status": 0, "trip_needed": o.trip_needed, "accept_bits": acc.numpy().view(np.uint32),
                 "track_counts": tc.numpy(), "trip_off": to.numpy(), "triplets": tr.numpy()[: o.trip_needed]}
         assert_same(host, ref, n * S, label=f"mode={mode}")
+
+
+def _z_table(w):
+    """The workload's layer planes as a geometry table: station z + (l - 1) dz."""
+    return np.array([np.float32(zs + (l - 1) * w.layer_dz) for zs in w.station_z for l in range(3)], np.float32)
+
+
+def _check_planar(b, table, S):
+    """Every hit of the generated batch lies on its layer's plane."""
+    layer = np.repeat(np.tile(np.arange(3 * S), b["n_events"]), np.diff(b["offsets"]))
+    assert np.array_equal(b["z"], table[layer])
+
+
+@pytest.mark.parametrize("workload,n", [("poisson20_1k", 1000), ("lognormal_timeslices", 1500)])
+def test_geometry_z_table_device(lib, synth_mod, workload, n):
+    # z = NULL with a per-layer table: the library fills per-hit z on the
+    # device and the results equal the run on the per-hit z array
+    import torch
+    w = synth_mod.WORKLOADS[workload]
+    S = w.n_stations
+    b = synth_mod.generate(w, 0, n)
+    table = _z_table(w)
+    _check_planar(b, table, S)
+    ctx = _ctx(lib, S, 1)
+    ref = gpu_select(ctx, b)
+    d = {k: torch.from_numpy(b[k]).cuda() for k in ("x", "y", "offsets")}
+    zt = torch.from_numpy(table).cuda()
+    for form in ("plain", "batched"):
+        r = ctx.select(d["x"], d["y"], None, d["offsets"], n, form=form, z_layer=zt)
+        torch.cuda.synchronize()
+        got = {"status": r["status"], "trip_needed": r["trip_needed"],
+               "accept_bits": r["accept_bits"].cpu().numpy().view(np.uint32),
+               "track_counts": r["track_counts"].cpu().numpy(), "trip_off": r["trip_off"].cpu().numpy(),
+               "triplets": r["triplets"].cpu().numpy()}
+        assert_same(got, ref, n * S, label=form)
+
+
+@pytest.mark.parametrize("n", [2000, 140_000])
+def test_geometry_z_table_host(lib, synth_mod, n):
+    # jpsi_run_host with z = NULL: 8 bytes per hit uploaded and z filled on the
+    # device (one piece, and per chunk on the pipelined path for >= 131072 events)
+    w = synth_mod.WORKLOADS["poisson20_1k"]
+    b = synth_mod.generate(w, 0, n)
+    table = _z_table(w)
+    _check_planar(b, table, 4)
+    ctx = _ctx(lib)
+    dev = gpu_select(ctx, b)
+    acc = np.zeros((n + 31) // 32, np.uint32)
+    tc = np.zeros(n, np.int32)
+    to = np.zeros(n * 4 + 1, np.int64)
+    tr = np.zeros((dev["trip_needed"] + 5, 3), np.int32)
+    o = lib.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off, o.triplets = acc.ctypes.data, tc.ctypes.data, to.ctypes.data, tr.ctypes.data
+    o.trip_capacity = len(tr)
+    hb = lib.make_batch(b["x"], b["y"], None, b["offsets"], n, b["n_hits"], z_layer=table)
+    for _ in range(2):
+        s = lib.jpsi_run_host(ctx.ctx, hb, o, 0)
+        assert s == 0, lib.jpsi_strerror(s)
+        host = {"status": 0, "trip_needed": o.trip_needed, "accept_bits": acc, "track_counts": tc, "trip_off": to,
+                "triplets": tr[: o.trip_needed]}
+        assert_same(host, dev, n * 4)
+    # no z and no table: refused
+    hb = lib.make_batch(b["x"], b["y"], None, b["offsets"], n, b["n_hits"])
+    assert lib.jpsi_run_host(ctx.ctx, hb, o, 0) == lib.JPSI_EINVAL
