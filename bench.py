@@ -659,6 +659,8 @@ def main():
                    "l2": f"inputs ({12 * n_hits / 1e9:.1f} GB) larger than L2; no flush", "seed": w.seed,
                    "launch_shape": shape},
         "hits_per_s": world * n_hits / (ms_b / 1000.0),
+        "median_step": {"events_per_s": world * n_ev / (per_sorted[len(per_sorted) // 2] / 1000.0),
+                        "hits_per_s": world * n_hits / (per_sorted[len(per_sorted) // 2] / 1000.0)},
         "plain": {"value": world * n_ev / (ms_p / 1000.0), "ms_per_step": ms_p},
         "latency_ms": {"p50": per_sorted[len(per_sorted) // 2],
                        "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
