@@ -500,7 +500,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=50_000, help="events per batch (stress workload)")
     ap.add_argument("--stress-budget-gb", type=int, default=160)
     ap.add_argument("--pool", type=int, default=8, help="distinct timeslices generated for the stream workload")
-    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--slots", type=int, default=5)
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     args = ap.parse_args()
     rank, world, local = dist_info()
