@@ -722,37 +722,74 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
     return count;
 }
 
+// Tile positions of a cell window, row by row: the first row's run [a, e)
+// is given; windows of more than one row continue on the next rows (each
+// row's columns [x0, x1] are one run of positions).
+template <int NX, int NY>
+struct WinIter {
+    int p, end, row, y1, x0, x1;
+    const uint16_t* bs;
+    __device__ __forceinline__ WinIter(int a, int e, const uint16_t* b, const Win& w) : p(a), end(e) {
+        if constexpr (NY > 1) {
+            bs = b;
+            row = w.y0;
+            y1 = w.y1;
+            x0 = w.x0;
+            x1 = w.x1;
+            settle();
+        }
+    }
+    __device__ __forceinline__ void settle() {
+        if constexpr (NY > 1) {
+            while (p >= end && row < y1) {
+                ++row;
+                p = bs[row * NX + x0];
+                end = bs[row * NX + x1 + 1];
+            }
+        }
+    }
+    __device__ __forceinline__ bool valid() const { return p < end; }
+    __device__ __forceinline__ void next() {
+        ++p;
+        settle();
+    }
+};
+
 // Does the staged station hold a passing triplet compatible with the
 // trigger slopes (mx, my)?  Per-thread search through each layer's cells
-// inside the tube: one run of positions from the window's first cell to its
-// last (a superset when the window spans rows).
+// inside the tube, row by row.
 template <class TV>
 __device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float my) {
-    int a[3], e[3];
+    Win w[3];
+    int a[3], e[3];  // first-row runs
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         const float b = t.meta[l].bmax;
-        const Win w = cell_window(t, l, mx, my, __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx))),
-                                  __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my))));
+        w[l] = cell_window(t, l, mx, my, __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx))),
+                           __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my))));
         const uint16_t* bs = t.bst + l * TV::NC;
-        a[l] = bs[w.y0 * TV::NX + w.x0];
-        e[l] = bs[w.y1 * TV::NX + w.x1 + 1];
+        a[l] = bs[w[l].y0 * TV::NX + w[l].x0];
+        e[l] = bs[w[l].y0 * TV::NX + w[l].x1 + 1];
     }
+    const uint16_t *bs0 = t.bst, *bs1 = t.bst + TV::NC, *bs2 = t.bst + 2 * TV::NC;
     const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     const float b0 = t.meta[0].bmax, b1 = t.meta[1].bmax, b2 = t.meta[2].bmax;
-    for (int p0 = a[0]; p0 < e[0]; ++p0) {
+    for (WinIter<TV::NX, TV::NY> i0(a[0], e[0], bs0, w[0]); i0.valid(); i0.next()) {
+        const int p0 = i0.p;
         const float2 P0 = t.P[p0];
         if (!tube_ok(P0.x, P0.y, b0, mx, my)) continue;
         const int h0 = base0 + t.idx[p0];
         const float x0 = __ldg(j.x + h0), y0 = __ldg(j.y + h0), z0 = __ldg(j.z + h0);
         if (!tube_pass(x0, y0, z0, mx, my, c)) continue;
-        for (int p1 = a[1]; p1 < e[1]; ++p1) {
+        for (WinIter<TV::NX, TV::NY> i1(a[1], e[1], bs1, w[1]); i1.valid(); i1.next()) {
+            const int p1 = i1.p;
             const float2 P1 = t.P[p1];
             if (!tube_ok(P1.x, P1.y, b1, mx, my)) continue;
             const int h1 = base1 + t.idx[p1];
             const float x1 = __ldg(j.x + h1), y1 = __ldg(j.y + h1), z1 = __ldg(j.z + h1);
             if (!tube_pass(x1, y1, z1, mx, my, c)) continue;
-            for (int p2 = a[2]; p2 < e[2]; ++p2) {
+            for (WinIter<TV::NX, TV::NY> i2(a[2], e[2], bs2, w[2]); i2.valid(); i2.next()) {
+                const int p2 = i2.p;
                 const float2 P2 = t.P[p2];
                 if (!tube_ok(P2.x, P2.y, b2, mx, my)) continue;
                 const int h2 = base2 + t.idx[p2];
