@@ -122,37 +122,91 @@ typedef struct jpsi_ctx jpsi_ctx;
 
 /* Creates a context on `device`.  hbm_budget bounds the bytes of device
  * scratch the context may hold (0 = 8 GiB).  The context owns its scratch
- * (per-unit counts, scan buffers, work queues, graphs, serving slots). */
+ * (per-unit counts, scan buffers, work queues, graphs, serving slots).  The
+ * paper's CUDA program allocates device memory for every batch before it
+ * copies the events over (Sec. 5.3); a context keeps that memory across
+ * runs instead.  JPSI_EINVAL for bad parameters or device number, JPSI_ECUDA
+ * without a usable device, JPSI_ENOMEM if its control blocks cannot be
+ * allocated; *out is NULL unless JPSI_OK. */
 jpsi_status jpsi_create(const jpsi_params *params, int device, size_t hbm_budget, jpsi_ctx **out);
 
-/* Releases everything the context owns.  NULL is ignored. */
+/* Releases everything the context owns (it first stops serving and waits
+ * for the device).  NULL is ignored.  No counterpart in the paper. */
 void jpsi_destroy(jpsi_ctx *ctx);
 
-/* One-launch form (Sec. 5.3's one-thread-per-event scheme recast as one warp
- * per event): a static grid with one warp per event; events too large for a
- * warp's shared-memory tile go to a block-per-event kernel.  `batch` and
- * `out` point to device memory.  `cuda_stream` is a cudaStream_t (NULL =
- * legacy default stream). */
+/* One-launch form: Sec. 5.3's kernel with one thread per event, recast as a
+ * static grid with one warp per event, plus a static grid with one block per
+ * event for the events too large for a warp's shared-memory tile (the block
+ * of an event the warp finished returns at once).  No event lists, work
+ * queues or graphs: the baseline the batched form is measured against.
+ * `batch` and `out` point to device memory.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream). */
 jpsi_status jpsi_run_plain(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
 
-/* Batched form: persistent kernels over an atomic work queue, events split
- * into light (warp) and heavy (block) work by the autotuned thresholds, the
- * counting passes replayed from a captured CUDA graph.  Same contract and
- * bit-identical results as jpsi_run_plain. */
+/* Batched form of Sec. 3.2 steps 1-3 over a batch of events (the paper
+ * times batches of 10^3 to 8*10^4 events per kernel, Table 1): persistent
+ * kernels over atomic work queues, events split between warp tiles, the
+ * block tile and the unpruned kernel by their size (jpsi_tuning), the phases
+ * replayed from captured CUDA graphs.  `batch` and `out` point to device
+ * memory; `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Same contract and bit-identical results as jpsi_run_plain. */
 jpsi_status jpsi_run(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
 
 /* jpsi_run on HOST memory: `batch` and `out` point to host buffers (pinned
  * for full speed).  The library copies inputs into device buffers it keeps
- * resident, runs, and copies the outputs back before returning. */
+ * resident, runs, and copies the outputs back before returning; Sec. 5.3
+ * copies the events to the GPU and the selected events back, and Table 1
+ * reports that transfer beside the kernel time.  Batches of at least 131,072
+ * events in CHAIN mode are copied in chunks while earlier chunks are counted
+ * (the paper notes that the transfer can be overlapped with computation); in
+ * PAPER mode, pinned inputs are read in place and only the trigger station
+ * crosses the link (the paper's host-side trigger filtering, Sec. 5.3).
+ * Errors as for jpsi_run. */
 jpsi_status jpsi_run_host(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
 
-/* Picks the batched form's launch shape (warps per block, events per grab,
- * light/heavy cutoff) by timing candidates on `sample` (device memory) and
- * keeps the fastest in the context.  Results do not depend on the choice. */
+/* How a context maps the work onto the GPU.  The paper has no counterpart
+ * (its one kernel has one thread per event, Sec. 5.3); none of these knobs
+ * changes a result.
+ *   light_wpb          warps per block of the small warp-tile kernel: 2, 4 or 8.
+ *   light_grab         events a persistent warp takes per atomic grab: 1 .. 64.
+ *   small_layer_cap    most hits in any layer of a processed station for an
+ *                      event to stay on the small warp tile: 1 .. 192.
+ *   medium_layer_cap   the same for the medium warp tile: 1 .. 384; events
+ *                      beyond both go to the block tile (or, past its limits,
+ *                      to the unpruned kernel).
+ *   heavy_ctas_per_sm  persistent block-tile CTAs per SM: 0 = as many as fit,
+ *                      else 1 .. that many.
+ *   record_cap         triplet rows the counting pass may record for the
+ *                      scatter: -1 = as needed within the budget, 0 = none
+ *                      (rows are then written by a second enumeration),
+ *                      > 0 = at most that many.
+ * jpsi_set_tuning returns JPSI_EINVAL for a value out of range and then
+ * changes nothing. */
+typedef struct {
+    int32_t light_wpb;
+    int32_t light_grab;
+    int32_t small_layer_cap;
+    int32_t medium_layer_cap;
+    int32_t heavy_ctas_per_sm;
+    int32_t reserved; /* 0 */
+    int64_t record_cap;
+} jpsi_tuning;
+jpsi_status jpsi_get_tuning(const jpsi_ctx *ctx, jpsi_tuning *out);
+jpsi_status jpsi_set_tuning(jpsi_ctx *ctx, const jpsi_tuning *tuning);
+
+/* Picks the batched form's tuning (warps per block and events per grab of the
+ * small warp tile, the small and medium tiles' layer cutoffs, block-tile CTAs
+ * per SM) by timing candidates on `sample` (device memory) and keeps the
+ * fastest in the context; record_cap is left as it is.  No counterpart in
+ * the paper.  Results do not depend on the choice.  If no candidate ran, the
+ * previous tuning is kept and the first failed run's status is returned.
+ * JPSI_EBUSY while serving (the slots' graphs are fixed). */
 jpsi_status jpsi_autotune(jpsi_ctx *ctx, const jpsi_batch *sample);
 
 /* ------------------------------------------------------------ serving
- * Continuous batching of timeslices.  jpsi_serve_start reserves `n_slots`
+ * Continuous batching of timeslices; no counterpart in the paper, whose
+ * Outlook (Sec. 8) only anticipates a free-streaming data flow.
+ * jpsi_serve_start reserves `n_slots`
  * resident slots whose device buffers fit `slot_hits` hits, `slot_events`
  * events and `slot_triplets` triplets each, within the context's budget.
  * jpsi_serve_submit copies one HOST batch into a free slot on a copy stream
@@ -171,7 +225,8 @@ jpsi_status jpsi_serve_wait(jpsi_ctx *ctx, uint64_t ticket, int timeout_ms, jpsi
                             double *latency_s);
 jpsi_status jpsi_serve_stop(jpsi_ctx *ctx);
 
-/* Device-time accounting of runs, for roofline measurements.  While enabled,
+/* Device-time accounting of runs, for roofline measurements (the paper times
+ * its kernel and the transfers separately, Table 1).  While enabled,
  * each run records CUDA events on its stream around its phases: the
  * warp-per-event counting kernel (light_ms), the rest of the counting phase
  * (block-per-event kernel, accept bits, scan: count_rest_ms) and the
@@ -221,10 +276,11 @@ jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);
 jpsi_status jpsi_select_noalloc(const jpsi_params *params, const jpsi_batch *batch, int32_t *track_counts,
                                 int32_t *unit_counts, void *cuda_stream);
 
-/* Static description of a status code. */
+/* Static description of a status code (no counterpart in the paper). */
 const char *jpsi_strerror(jpsi_status status);
 
-/* Detail of the last error seen on this context (empty if none). */
+/* Detail of the last error seen on this context (empty if none; no
+ * counterpart in the paper). */
 const char *jpsi_last_error(const jpsi_ctx *ctx);
 
 #ifdef __cplusplus

@@ -21,7 +21,8 @@ JPSI_MODE_PAPER, JPSI_MODE_CHAIN = 0, 1
 # every symbol include/jpsi.h declares
 EXPORTS = ("jpsi_create", "jpsi_destroy", "jpsi_run_plain", "jpsi_run", "jpsi_run_host", "jpsi_autotune",
            "jpsi_serve_start", "jpsi_serve_submit", "jpsi_serve_wait", "jpsi_serve_stop", "jpsi_strerror",
-           "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get", "jpsi_select_noalloc")
+           "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get", "jpsi_select_noalloc", "jpsi_get_tuning",
+           "jpsi_set_tuning")
 
 
 class JpsiError(RuntimeError):
@@ -51,6 +52,15 @@ class jpsi_timing(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("light_ms", ctypes.c_double),
                 ("count_rest_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
                 ("light_wpb", ctypes.c_int32), ("light_grab", ctypes.c_int32)]
+
+
+class jpsi_tuning(ctypes.Structure):
+    _fields_ = [("light_wpb", ctypes.c_int32), ("light_grab", ctypes.c_int32), ("small_layer_cap", ctypes.c_int32),
+                ("medium_layer_cap", ctypes.c_int32), ("heavy_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("record_cap", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 _lib = None
@@ -97,6 +107,10 @@ def load(build_if_missing: bool = False):
     lib.jpsi_timing_get.restype = st
     lib.jpsi_select_noalloc.argtypes = [P(jpsi_params), P(jpsi_batch), vp, vp, vp]
     lib.jpsi_select_noalloc.restype = st
+    lib.jpsi_get_tuning.argtypes = [vp, P(jpsi_tuning)]
+    lib.jpsi_get_tuning.restype = st
+    lib.jpsi_set_tuning.argtypes = [vp, P(jpsi_tuning)]
+    lib.jpsi_set_tuning.restype = st
     _lib = lib
     return lib
 
@@ -176,6 +190,18 @@ def jpsi_timing_get(ctx) -> jpsi_timing:
     if s != JPSI_OK:
         raise JpsiError(s, "jpsi_timing_get")
     return t
+
+
+def jpsi_get_tuning(ctx) -> jpsi_tuning:
+    t = jpsi_tuning()
+    s = load().jpsi_get_tuning(ctx, ctypes.byref(t))
+    if s != JPSI_OK:
+        raise JpsiError(s, "jpsi_get_tuning")
+    return t
+
+
+def jpsi_set_tuning(ctx, t: jpsi_tuning) -> int:
+    return load().jpsi_set_tuning(ctx, ctypes.byref(t))
 
 
 def jpsi_select_noalloc(params: jpsi_params, batch: jpsi_batch, track_counts, unit_counts, stream=0) -> int:

@@ -98,7 +98,7 @@ struct jpsi_ctx {
     bool pageable_ok = false;
     float cx = 0, cy = 0, K = 0;
     LaunchCfg plain_cfg, batch_cfg;
-    int grab = 2;
+    jpsi_tuning tune{4, 2, 192, 384, 0, 0, -1};
     int cfg_id = 0;  // bumps when the launch shape changes (graphs re-captured)
     cudaStream_t cap_stream = nullptr;
     cudaStream_t copy_stream = nullptr;  // host-to-device copies of jpsi_run_host
@@ -264,7 +264,9 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.cx = c->cx;
     j.cy = c->cy;
     j.K = c->K;
-    j.grab = c->grab;
+    j.grab = c->tune.light_grab;
+    j.cap_small = c->tune.small_layer_cap;
+    j.cap_medium = c->tune.medium_layer_cap;
     j.host_hits = host_hits ? 1 : 0;
     j.unit_counts = (int32_t*)rs.unit_counts.p;
     j.track_counts = o->track_counts ? o->track_counts : (int32_t*)rs.track_counts.p;
@@ -285,14 +287,19 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.triplets = o->triplets;
     j.tscr = nullptr;
     j.tscr_cap = 0;
-    if (o->triplets) {
+    if (o->triplets && c->tune.record_cap != 0) {
         // entries of the counting pass; without room for them the triplets are
-        // written by re-enumeration instead (same result, slower)
-        const size_t want = (size_t)std::min<int64_t>(rs.tscr_want, std::max<int64_t>(o->trip_capacity, 1)) * sizeof(TripEntry);
+        // written by re-enumeration instead (same result, slower).  Entries
+        // also come from paths that later hand their event on, so the record
+        // may need a little more than the run's triplets.
+        const int64_t cap = std::max<int64_t>(o->trip_capacity, 1);
+        int64_t n_want = std::min<int64_t>(rs.tscr_want, cap + cap / 4 + 4096);
+        if (c->tune.record_cap > 0) n_want = std::min<int64_t>(n_want, c->tune.record_cap);
+        const size_t want = (size_t)n_want * sizeof(TripEntry);
         const bool fits = want <= rs.tscr.bytes || c->used + (want - rs.tscr.bytes) <= c->budget;
         if (fits && ensure(c, rs.tscr, want, "triplet entries") == JPSI_OK) {
             j.tscr = (TripEntry*)rs.tscr.p;
-            j.tscr_cap = (int64_t)(rs.tscr.bytes / sizeof(TripEntry));
+            j.tscr_cap = (int64_t)std::min<size_t>(rs.tscr.bytes / sizeof(TripEntry), (size_t)n_want);
         }
     }
     j.ctrl = rs.d_ctrl;
@@ -435,20 +442,19 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         b = &bz;
     }
     if ((s = prepare(c, rs, b, o, host_hits)) != JPSI_OK) return s;
-    const int64_t ne = b->n_events, nu = ne * c->p.n_stations;
+    const int64_t ne = b->n_events;
     cudaError_t e;
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
     const bool timing = c->timing.load();
     if (batched && (s = capture_graphs(c, rs)) != JPSI_OK) return s;
     if (timing) cudaEventRecord(rs.ev[0], st);
-    e = batched ? graph_launch(rs.g_light, rs.job, st) : launch_light_count(rs.job, ne, c->plain_cfg, false, st);
+    e = batched ? graph_launch(rs.g_light, rs.job, st) : launch_plain_light(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "light count");
     if (timing) cudaEventRecord(rs.ev[1], st);
-    e = batched ? graph_launch(rs.g_rest, rs.job, st) : launch_count_rest(rs.job, c->plain_cfg, st);
+    e = batched ? graph_launch(rs.g_rest, rs.job, st) : launch_plain_rest(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "count rest");
     if (timing) cudaEventRecord(rs.ev[2], st);
-    int launches = kLaunchesLight + kLaunchesRest;
-    (void)nu;
+    int launches = batched ? kLaunchesLight + kLaunchesRest : kLaunchesPlainLight + kLaunchesPlainRest;
     if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "ctrl readback");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "count phase");
@@ -476,10 +482,10 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     if (scattered)
         e = batched ? graph_launch(rs.g_scatter, rs.job, st) : launch_scatter(rs.job, c->plain_cfg, st);
     else
-        e = batched ? graph_launch(rs.g_emit, rs.job, st) : launch_emit_phase(rs.job, ne, c->plain_cfg, false, st);
+        e = batched ? graph_launch(rs.g_emit, rs.job, st) : launch_plain_emit(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "emit");
     if (timing) cudaEventRecord(rs.ev[4], st);
-    launches += scattered ? kLaunchesScatter : kLaunchesEmit;
+    launches += scattered ? kLaunchesScatter : batched ? kLaunchesEmit : kLaunchesPlainEmit;
     if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "ctrl readback");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "emit phase");
@@ -488,11 +494,13 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     return JPSI_OK;
 }
 
-void set_launch_shape(jpsi_ctx* c, int wpb, int grab) {
-    c->grab = grab;
+// Launch grids of the batched form from the context's tuning.
+void apply_tuning(jpsi_ctx* c) {
+    const int wpb = c->tune.light_wpb;
     const int lb = std::max(1, light_max_blocks_per_sm(wpb));
     const int gb = std::max(1, generic_max_blocks_per_sm(256));
-    const int hb = std::max(1, heavy_max_blocks_per_sm());
+    const int hmax = std::max(1, heavy_max_blocks_per_sm());
+    const int hb = c->tune.heavy_ctas_per_sm > 0 ? std::min(c->tune.heavy_ctas_per_sm, hmax) : hmax;
     const int mb = std::max(1, medium_max_blocks_per_sm());
     c->batch_cfg.light_wpb = wpb;
     c->batch_cfg.light_blocks = c->n_sm * lb;
@@ -614,6 +622,17 @@ jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_
     return s;
 }
 
+// Between the chunks of a pipelined counting pass: the work counters start
+// again, and the next chunk's list entries start where this chunk's end (its
+// events are appended behind them, so the lists end up covering the batch).
+cudaError_t next_pass_lists(RunState& rs, cudaStream_t st) {
+    static_assert(offsetof(Ctrl, m_begin) == offsetof(Ctrl, n_medium) + 3 * sizeof(int32_t), "list fields");
+    cudaError_t e = cudaMemsetAsync(rs.d_ctrl->work, 0, sizeof(rs.d_ctrl->work), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&rs.d_ctrl->m_begin, &rs.d_ctrl->n_medium, 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
 // jpsi_run_host for large batches: the hits go to the device chunk by chunk
 // on the copy stream while the warp kernels count the chunks that have
 // arrived (events [ev_begin, ev_begin + ev_count) of the batch); accept bits,
@@ -684,7 +703,6 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         if (e == cudaSuccess) e = cudaEventRecord(rs.chunk_ev[k], c->copy_stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "chunk upload");
-    const size_t ctr_off = offsetof(Ctrl, n_medium), ctr_len = offsetof(Ctrl, trip_total) - ctr_off;
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
     k = 0;
     for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
@@ -695,7 +713,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         if ((e = cudaStreamWaitEvent(st, rs.chunk_ev[k], 0)) != cudaSuccess ||
             (ztable && (e = launch_expand_z((const int32_t*)c->hoff.p, (const float*)rs.ztab.p, (float*)c->hz.p, e0,
                                             e1, (int)S, hb->n_hits, c->n_sm, st)) != cudaSuccess) ||
-            (k > 0 && (e = cudaMemsetAsync((char*)rs.d_ctrl + ctr_off, 0, ctr_len, st)) != cudaSuccess) ||
+            (k > 0 && (e = next_pass_lists(rs, st)) != cudaSuccess) ||
             (e = launch_light_count(jk, e1 - e0, c->batch_cfg, true, st)) != cudaSuccess ||
             (e = launch_count_lists(jk, c->batch_cfg, st)) != cudaSuccess)
             return cuda_fail(c, e, "chunk count");
@@ -716,7 +734,9 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
                                ctl.scratch_n <= (unsigned long long)all.tscr_cap;
         if (!scattered && all.tscr && !(ctl.status & kStNoScratch))
             rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
-        e = scattered ? launch_scatter(all, c->batch_cfg, st) : launch_emit_phase(all, ne, c->batch_cfg, true, st);
+        if (!scattered) e = cudaMemsetAsync(&rs.d_ctrl->m_begin, 0, 3 * sizeof(int32_t), st);  // every chunk's events
+        if (e == cudaSuccess)
+            e = scattered ? launch_scatter(all, c->batch_cfg, st) : launch_emit_phase(all, ne, c->batch_cfg, true, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "emit");
@@ -788,7 +808,7 @@ jpsi_status jpsi_create(const jpsi_params* params, int device, size_t hbm_budget
         jpsi_destroy(c);
         return JPSI_ENOMEM;
     }
-    set_launch_shape(c, 4, 2);
+    apply_tuning(c);
     *out = c;
     return JPSI_OK;
 }
@@ -867,7 +887,29 @@ jpsi_status jpsi_timing_get(jpsi_ctx* c, jpsi_timing* out) {
     std::lock_guard<std::mutex> lk(c->err_mu);
     *out = c->tm;
     out->light_wpb = c->batch_cfg.light_wpb;
-    out->light_grab = c->grab;
+    out->light_grab = c->tune.light_grab;
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_get_tuning(const jpsi_ctx* c, jpsi_tuning* out) {
+    if (!c || !out) return JPSI_EINVAL;
+    *out = c->tune;
+    return JPSI_OK;
+}
+
+jpsi_status jpsi_set_tuning(jpsi_ctx* c, const jpsi_tuning* t) {
+    if (!c || !t) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    if (c->serving) return fail(c, JPSI_EBUSY, "tuning is fixed while serving");
+    cudaSetDevice(c->device);
+    const bool ok = (t->light_wpb == 2 || t->light_wpb == 4 || t->light_wpb == 8) && t->light_grab >= 1 &&
+                    t->light_grab <= 64 && t->small_layer_cap >= 1 && t->small_layer_cap <= 192 &&
+                    t->medium_layer_cap >= 1 && t->medium_layer_cap <= 384 && t->heavy_ctas_per_sm >= 0 &&
+                    t->heavy_ctas_per_sm <= heavy_max_blocks_per_sm() && t->reserved == 0 && t->record_cap >= -1;
+    if (!ok) return fail(c, JPSI_EINVAL, "tuning value out of range");
+    c->tune = *t;
+    apply_tuning(c);
     return JPSI_OK;
 }
 
@@ -875,6 +917,7 @@ jpsi_status jpsi_autotune(jpsi_ctx* c, const jpsi_batch* sample) {
     if (!c) return JPSI_EINVAL;
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    if (c->serving) return fail(c, JPSI_EBUSY, "tuning is fixed while serving");
     cudaSetDevice(c->device);
     c->last_error.clear();
     jpsi_outputs o{};
@@ -884,39 +927,77 @@ jpsi_status jpsi_autotune(jpsi_ctx* c, const jpsi_batch* sample) {
     if ((s = ensure(c, acc, (size_t)std::max<int64_t>((sample->n_events + 31) / 32, 1) * 4, "autotune"))) return s;
     o.accept_bits = (uint32_t*)acc.p;
     cudaStream_t st = c->cap_stream;
-    const int wpbs[] = {2, 4, 8};
-    const int grabs[] = {1, 2, 4, 8};
-    float best = INFINITY;
-    int bw = 4, bg = 2;
     cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    for (int w : wpbs) {
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        release(c, acc);
+        return fail(c, JPSI_ECUDA, "event creation failed");
+    }
+    const jpsi_tuning start = c->tune;
+    jpsi_tuning best = start;
+    float best_ms = INFINITY;
+    jpsi_status first_err = JPSI_OK;
+    // device time of three runs of the sample after one warm-up run (graph
+    // capture, scratch growth); false if a run failed
+    auto trial = [&](const jpsi_tuning& t) {
+        c->tune = t;
+        apply_tuning(c);
+        float tot = 0;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            const jpsi_status r = run_device(c, c->rs, sample, &o, st, true);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            if (r != JPSI_OK) {
+                if (first_err == JPSI_OK) first_err = r;
+                return;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = t;
+        }
+    };
+    // one dimension at a time, each from the best shape so far
+    for (int w : {2, 4, 8}) {
         if (light_max_blocks_per_sm(w) < 1) continue;
-        for (int gr : grabs) {
-            set_launch_shape(c, w, gr);
-            float tot = 0;
-            bool ok = true;
-            for (int rep = 0; rep < 4 && ok; ++rep) {
-                cudaEventRecord(e0, st);
-                ok = run_device(c, c->rs, sample, &o, st, true) == JPSI_OK;
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tot += ms;  // first run warms up / captures
-            }
-            if (ok && tot < best) {
-                best = tot;
-                bw = w;
-                bg = gr;
-            }
+        for (int gr : {1, 2, 4, 8}) {
+            jpsi_tuning t = best;
+            t.light_wpb = w;
+            t.light_grab = gr;
+            trial(t);
+        }
+    }
+    if (best_ms < INFINITY) {
+        const jpsi_tuning b1 = best;
+        for (int cap : {96, 128, 160, 192}) {
+            jpsi_tuning t = b1;
+            t.small_layer_cap = cap;
+            if (cap != b1.small_layer_cap) trial(t);
+        }
+        const jpsi_tuning b2 = best;
+        for (int cap : {256, 320, 384}) {
+            jpsi_tuning t = b2;
+            t.medium_layer_cap = cap;
+            if (cap != b2.medium_layer_cap) trial(t);
+        }
+        const jpsi_tuning b3 = best;
+        const int hmax = heavy_max_blocks_per_sm();
+        for (int h = 1; h <= hmax; ++h) {
+            jpsi_tuning t = b3;
+            t.heavy_ctas_per_sm = h;
+            if (h != (b3.heavy_ctas_per_sm > 0 ? b3.heavy_ctas_per_sm : hmax)) trial(t);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     release(c, acc);
-    set_launch_shape(c, bw, bg);
+    const bool any = best_ms < INFINITY;
+    c->tune = any ? best : start;
+    apply_tuning(c);
+    if (!any) return fail(c, first_err != JPSI_OK ? first_err : JPSI_ECUDA, "autotune: no candidate ran");
     return JPSI_OK;
 }
 

@@ -30,12 +30,20 @@ constexpr int32_t kPackLimit = 1 << 20;
 // Event classes (Job::ev_class).
 enum : uint8_t { kClsLight = 0, kClsHeavy = 1, kClsInvalid = 2, kClsGeneric = 3, kClsMedium = 4 };
 
-// Device-resident control block of one run (zeroed before each run).
+// Device-resident control block of one run (zeroed before each run).  The
+// three event lists grow over the whole run: a run counted chunk by chunk
+// appends every chunk's events behind the previous chunk's, and each
+// counting pass takes the list entries from its *_begin on (the emit pass
+// over the whole batch starts them at 0 again).
 struct Ctrl {
     int32_t status;
     int32_t n_medium;             // events sent to the medium warp kernel
     int32_t n_heavy;              // events sent to the block-tile kernel
     int32_t n_generic;            // events sent to the unpruned block kernel
+    int32_t m_begin;              // first medium / block-tile / unpruned list entry
+    int32_t h_begin;              //   of the current pass (same order as the
+    int32_t g_begin;              //   three counts above)
+    int32_t pad_;
     // persistent work counters: small, medium, heavy, generic (count); same
     // (emit); [8] per-station units of the block-tile path (count)
     unsigned long long work[10];
@@ -58,7 +66,9 @@ struct Job {
     int32_t S, trig, mode, minc;
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
+    int32_t cap_small, cap_medium;// most hits per layer on the small / medium warp tile (<= the tile's own)
     int32_t persistent;           // warp kernels: persistent warps (1) or one warp per event (0)
+    int32_t plain;                // one-launch form: no event lists (events carry their class only)
     int32_t host_hits;            // x, y, z, off are pinned host memory read over the link: no L2 prefetch
     int32_t* unit_counts;         // [n_events*S]
     int32_t* track_counts;        // [n_events]
@@ -112,6 +122,13 @@ constexpr int kLaunchesScatter = 1;
 // re-enumerate their units and write rows at trip_off.
 cudaError_t launch_emit_phase(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
                               cudaStream_t st);
+// One-launch form (no lists, queues or graphs): the static warp grid (1
+// launch), then the static block-per-event grid and the tail (1 + 4); its
+// emit fallback is the two static grids again (2).
+cudaError_t launch_plain_light(const Job& j, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_plain_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
+cudaError_t launch_plain_emit(const Job& j, const LaunchCfg& lc, cudaStream_t st);
+constexpr int kLaunchesPlainLight = 1, kLaunchesPlainRest = 5, kLaunchesPlainEmit = 2;
 // Per-hit z of events [ev0, ev1) from a per-layer table z_layer[S*3] (device
 // pointers; one launch).
 cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, int64_t ev0, int64_t ev1, int S,

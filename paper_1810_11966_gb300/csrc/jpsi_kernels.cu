@@ -70,15 +70,15 @@ struct WCfg {
     static constexpr int WPB = WPB_;                // warps per block (medium: fixed)
 };
 using SmallCfg = WCfg<6, 384, 64, 1, kClsLight, 0>;      // 192 hits/layer, 384/station
-using MediumCfg = WCfg<12, 960, 128, 2, kClsMedium, 4>;  // 384 hits/layer, 960/station
+using MediumCfg = WCfg<12, 960, 32, 16, kClsMedium, 4>;  // 384 hits/layer, 960/station
 
 // block-tile path
 constexpr int kHThreads = 256;
 constexpr int kHWarps = kHThreads / 32;
 constexpr int kHRMax = 8;                         // hits per thread per layer
 constexpr int kHLayerCap = kHThreads * kHRMax;    // 2048 hits per layer
-constexpr int kHHCap = 6144;                      // hits per station tile
-constexpr int kNXH = 128, kNYH = 4;               // slope bins per layer in s_x, s_y
+constexpr int kHHCap = 5632;                      // hits per station tile
+constexpr int kNXH = 64, kNYH = 32;               // slope bins per layer in s_x, s_y
 constexpr int kNCH = kNXH * kNYH;                 // cells per layer
 
 struct LayerMeta {
@@ -105,24 +105,18 @@ template <class Cfg>
 struct WarpTile {
     float2 P[Cfg::HCAP];
     uint16_t idx[Cfg::HCAP];
-    union {
-        uint32_t queue[kQCap];  // pair queue (enumeration)
-        uint32_t hist[Cfg::NC]; // cell counts of the layer being staged (staging)
-    };
+    uint32_t queue[kQCap];      // pair queue (enumeration)
     float2 T[kTCap];            // trigger triplet slopes
     uint8_t alive[kTCap];
-    uint16_t bst[3 * Cfg::NC + 1];
+    alignas(4) uint16_t bst[3 * Cfg::NC + 1];  // cell starts (cell counts while a layer is staged)
     LayerMeta meta[3];
 };
 
 struct HeavySmem {
     float2 P[kHHCap];
     uint16_t idx[kHHCap];
-    union {
-        uint32_t queue[kHWarps][kQCap];
-        uint32_t hist[kNCH];
-    };
-    uint16_t bst[3 * kNCH + 1];
+    uint32_t queue[kHWarps][kQCap];
+    alignas(4) uint16_t bst[3 * kNCH + 1];  // cell starts (cell counts while a layer is staged)
     LayerMeta meta[3];
     int32_t off[3 * kMaxStations + 1];
     int32_t wsum[kHWarps];
@@ -215,6 +209,16 @@ __device__ bool warp_load_offsets(const Job& j, int64_t e, int lane, EvOff& o) {
 
 // ------------------------------------------------------- warp staging
 
+// Cell histogram of the layer being staged, kept in place in the layer's own
+// cell-start array: two 16-bit counters per 32-bit word (a count never
+// exceeds the layer's hit capacity, < 2^16, so no carry crosses into the
+// neighbour).  Returns the hit's rank in its cell.
+__device__ __forceinline__ int cell_count_add(uint16_t* cnt, int cell) {
+    uint32_t* wd = reinterpret_cast<uint32_t*>(cnt) + (cell >> 1);
+    const int sh = (cell & 1) << 4;
+    return (int)((atomicAdd(wd, 1u << sh) >> sh) & 0xffffu);
+}
+
 // Stages one layer into the warp tile.  Returns 0, or 1 (z <= 0), or 2 (a
 // hit whose pruning bound is not finite).  Hits are counted into cells with
 // shared-memory atomics (the order inside a cell is not fixed; results do
@@ -226,10 +230,12 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     static_assert(NC % 32 == 0, "cells per layer");
     float sx[R], sy[R];
     int key[R];  // cell << 16 | rank in the cell once binned; -1: not stored
+    static_assert(CPL % 2 == 0, "two 16-bit cell counters per word");
     float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
     bool bad = false;
+    uint16_t* bst = w.bst + l * NC;  // the end of layer l is the start of layer l + 1
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) w.hist[CPL * lane + q] = 0;
+    for (int q = 0; q < CPL / 2; ++q) reinterpret_cast<uint32_t*>(bst)[CPL / 2 * lane + q] = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         key[r] = -1;
@@ -296,7 +302,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         if (key[r] >= 0) {
             const int row = NY > 1 ? slope_bin<NY>(sy[r], loy, scy) : 0;
             const int cell = row * NX + slope_bin<NX>(sx[r], lox, scx);
-            key[r] = (cell << 16) | (int)atomicAdd(&w.hist[cell], 1u);
+            key[r] = (cell << 16) | cell_count_add(bst, cell);
         }
     }
     __syncwarp();
@@ -305,12 +311,11 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
-        cs[q] = (int)w.hist[CPL * lane + q];
+        cs[q] = (int)bst[CPL * lane + q];
         cnt += cs[q];
     }
     const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    uint16_t* bst = w.bst + l * NC;  // the end of layer l is the start of layer l + 1
     int run = pbase + incl - cnt;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
@@ -369,10 +374,12 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     float sx[kHRMax], sy[kHRMax];
     int key[kHRMax];  // cell << 16 | rank in the cell once binned; -1: not stored
+    static_assert(CPT % 2 == 0, "two 16-bit cell counters per word");
     float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
+    uint16_t* bst = sm.bst + l * kNCH;  // the end of layer l is the start of layer l + 1
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) sm.hist[CPT * tid + q] = 0;
+    for (int q = 0; q < CPT / 2; ++q) reinterpret_cast<uint32_t*>(bst)[CPT / 2 * tid + q] = 0;
 #pragma unroll
     for (int r = 0; r < kHRMax; ++r) {
         key[r] = -1;
@@ -433,7 +440,7 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         if (kHThreads * r >= n) break;
         if (key[r] >= 0) {
             const int cell = slope_bin<kNYH>(sy[r], loy, scy) * kNXH + slope_bin<kNXH>(sx[r], lox, scx);
-            key[r] = (cell << 16) | (int)atomicAdd(&sm.hist[cell], 1u);
+            key[r] = (cell << 16) | cell_count_add(bst, cell);
         }
     }
     __syncthreads();
@@ -442,7 +449,7 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
-        cs[q] = (int)sm.hist[CPT * tid + q];
+        cs[q] = (int)bst[CPT * tid + q];
         cnt += cs[q];
     }
     const int incl = warp_incl_scan(cnt, lane);
@@ -454,7 +461,6 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         woff += q < wp ? sm.wsum[q] : 0;
         total += sm.wsum[q];
     }
-    uint16_t* bst = sm.bst + l * kNCH;  // the end of layer l is the start of layer l + 1
     int run = pbase + woff + incl - cnt;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
@@ -540,6 +546,7 @@ struct TSink {
     int cap;
     int* sh_n;  // block-shared counter, or null
     int n;      // warp-local counter when sh_n is null
+    bool norec = false;  // a repeated enumeration: record no triplet entries
 };
 
 // Items of up to 32 lanes laid end to end: lane i owns items [excl, excl +
@@ -643,7 +650,7 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
                     }
                     if (ok && tb + rk < ts.cap) ts.T[tb + rk] = make_float2(mx, my);
                 }
-                if (!EMIT && j.tscr) {  // record for the scatter pass
+                if (!EMIT && j.tscr && !ts.norec) {  // record for the scatter pass
                     unsigned long long b = 0;
                     if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)np);
                     b = __shfl_sync(kFull, b, 0) + rk;
@@ -663,6 +670,18 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
     __syncwarp();
 }
 
+template <class TV>
+__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, int lane);
+
+// CHAIN-mode trigger slopes a block searches for while it enumerates a
+// station (block path): item n_rounds + i of the block-shared counter is
+// slope i; a slope with no compatible triplet in the station loses its flag.
+struct RoadItems {
+    const float2* T;
+    uint8_t* alive;
+    int n;
+};
+
 // All passing triplets of the staged station (Sec. 3.2 steps 1-2) found by
 // this warp: rounds of 32 L0 hits (all of them, or those this warp takes
 // from a block-shared counter when the warps of a block share a station), each
@@ -671,9 +690,11 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
 // triplet are queued and drained against L2.
 template <bool EMIT, bool SHARED, class TV>
 __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane, const Cuts& c,
-                            TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int* sh_next) {
+                            TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int* sh_next,
+                            const RoadItems* rd = nullptr) {
     const int n0 = t.meta[0].nlive, n1 = t.meta[1].nlive, n2 = t.meta[2].nlive;
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
+    const int n_rounds = (n0 + 31) >> 5;
     const int p0 = t.meta[0].pbase;
     const float B01 = __fadd_rn(t.meta[0].bmax, t.meta[1].bmax);
     int qn = 0, count = 0;
@@ -685,7 +706,19 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
         return 32 * __shfl_sync(kFull, g, 0);
     };
     int i0 = 0;
-    if constexpr (SHARED) i0 = next_round();
+    if constexpr (SHARED) {
+        i0 = next_round();
+        // items past the rounds: trigger slopes to search for (CHAIN)
+        while (rd && i0 >= n0 && (i0 >> 5) - n_rounds < rd->n) {
+            const int ti = (i0 >> 5) - n_rounds;
+            if (rd->alive[ti]) {
+                const float2 m = rd->T[ti];
+                const bool found = road_warp(j, t, c, m.x, m.y, lane);
+                if (lane == 0 && !found) rd->alive[ti] = 0;
+            }
+            i0 = next_round();
+        }
+    }
     for (; i0 < n0;) {
         const bool has = i0 + lane < n0;
         const float2 Pi = t.P[p0 + (has ? i0 + lane : 0)];
@@ -712,10 +745,20 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
                 }
             }
         }
-        if constexpr (SHARED)
+        if constexpr (SHARED) {
             i0 = next_round();
-        else
+            while (rd && i0 >= n0 && (i0 >> 5) - n_rounds < rd->n) {
+                const int ti = (i0 >> 5) - n_rounds;
+                if (rd->alive[ti]) {
+                    const float2 m = rd->T[ti];
+                    const bool found = road_warp(j, t, c, m.x, m.y, lane);
+                    if (lane == 0 && !found) rd->alive[ti] = 0;
+                }
+                i0 = next_round();
+            }
+        } else {
             i0 += 32;
+        }
     }
     __syncwarp();
     drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
@@ -804,10 +847,89 @@ __device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float m
     return false;
 }
 
+// Warp-cooperative road(): the 32 lanes search together for one trigger
+// slope (mx, my warp-uniform).  For each layer they test the tube on the
+// window's tile positions, row by row, 32 at a time, and keep the hits that
+// pass tube_pass: the k-th kept hit of layer l sits in lane k's registers.
+// Every combination of one kept hit per layer then gets P1 and P2.  A layer
+// with more than 32 kept hits hands the slope to road() on one lane (no such
+// limit).  Same answer as road(), warp-uniform.
+template <class TV>
+__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, int lane) {
+    float hx[3] = {0.f, 0.f, 0.f}, hy[3] = {0.f, 0.f, 0.f}, hz[3] = {0.f, 0.f, 0.f};
+    int nk[3] = {0, 0, 0};
+    bool over = false;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const float b = t.meta[l].bmax;
+        const Win w = cell_window(t, l, mx, my, __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(mx))),
+                                  __fadd_rn(b, __fmul_rn(2.0f * kKappa, fabsf(my))));
+        const uint16_t* bs = t.bst + l * TV::NC;
+        const int32_t base = t.meta[l].base;
+        for (int row = w.y0; row <= w.y1 && !over; ++row) {
+            const int a = bs[row * TV::NX + w.x0], e = bs[row * TV::NX + w.x1 + 1];
+            for (int p0 = a; p0 < e; p0 += 32) {
+                const int p = p0 + lane;
+                bool keep = false;
+                float x = 0.f, y = 0.f, z = 0.f;
+                if (p < e) {
+                    const float2 P = t.P[p];
+                    if (tube_ok(P.x, P.y, b, mx, my)) {
+                        const int h = base + t.idx[p];
+                        x = __ldg(j.x + h);
+                        y = __ldg(j.y + h);
+                        z = __ldg(j.z + h);
+                        keep = tube_pass(x, y, z, mx, my, c);
+                    }
+                }
+                unsigned m = __ballot_sync(kFull, keep);
+                if (nk[l] + __popc(m) > 32) {
+                    over = true;
+                    break;
+                }
+                while (m) {  // the kept hits go to lanes nk, nk + 1, ...
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float vx = __shfl_sync(kFull, x, src), vy = __shfl_sync(kFull, y, src),
+                                vz = __shfl_sync(kFull, z, src);
+                    if (lane == nk[l]) {
+                        hx[l] = vx;
+                        hy[l] = vy;
+                        hz[l] = vz;
+                    }
+                    ++nk[l];
+                }
+            }
+        }
+        if (over) break;
+        if (nk[l] == 0) return false;
+    }
+    if (over) {
+        bool f = false;
+        if (lane == 0) f = road(j, t, c, mx, my);
+        return __shfl_sync(kFull, f, 0);
+    }
+    const int n01 = nk[0] * nk[1], total = n01 * nk[2];
+    for (int it0 = 0; it0 < total; it0 += 32) {
+        const int it = min(it0 + lane, total - 1);
+        const int i2 = it / n01, r = it - i2 * n01, i1 = r / nk[0], i0 = r - i1 * nk[0];
+        const float xs[3] = {__shfl_sync(kFull, hx[0], i0), __shfl_sync(kFull, hx[1], i1),
+                             __shfl_sync(kFull, hx[2], i2)};
+        const float ys[3] = {__shfl_sync(kFull, hy[0], i0), __shfl_sync(kFull, hy[1], i1),
+                             __shfl_sync(kFull, hy[2], i2)};
+        const float zs[3] = {__shfl_sync(kFull, hz[0], i0), __shfl_sync(kFull, hz[1], i1),
+                             __shfl_sync(kFull, hz[2], i2)};
+        float fx, fy;
+        if (__any_sync(kFull, fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c))) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------ warp path
 
 __device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls) {
     j.ev_class[e] = cls;
+    if (j.plain) return;  // the one-launch form's block kernel finds the event by its class
     if (cls == kClsMedium) {
         const int gi = atomicAdd(&j.ctrl->n_medium, 1);
         j.mlist[gi] = (int32_t)e;
@@ -821,15 +943,17 @@ __device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls)
 }
 
 // Does an event fit a warp tile of this shape (processed stations only)?
+// The tile's layer capacity may be lowered at run time (Job::cap_small,
+// cap_medium: a tuning choice, results do not depend on it).
 template <class Cfg>
 __device__ __forceinline__ bool fits_warp(const Job& j, const EvOff& o, int nproc) {
+    const int cap = min(Cfg::LAYER_CAP, Cfg::CLS == kClsLight ? j.cap_small : j.cap_medium);
     bool fits = true;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
         const int32_t o0 = off_get(o, 3 * s), o1 = off_get(o, 3 * s + 1), o2 = off_get(o, 3 * s + 2),
                       o3 = off_get(o, 3 * s + 3);
-        if (o1 - o0 > Cfg::LAYER_CAP || o2 - o1 > Cfg::LAYER_CAP || o3 - o2 > Cfg::LAYER_CAP || o3 - o0 > Cfg::HCAP)
-            fits = false;
+        if (o1 - o0 > cap || o2 - o1 > cap || o3 - o2 > cap || o3 - o0 > Cfg::HCAP) fits = false;
     }
     return fits;
 }
@@ -852,7 +976,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
     const int nproc = j.mode == 1 ? S : 1;
     if (!fits_warp<Cfg>(j, o, nproc)) {
         // all lanes take part in the shuffles of the size check
-        const bool to_medium = kSmall && fits_warp<MediumCfg>(j, o, nproc);
+        const bool to_medium = kSmall && !j.plain && fits_warp<MediumCfg>(j, o, nproc);
         if (lane == 0) push_event(j, e, to_medium ? kClsMedium : kClsHeavy);
         return;
     }
@@ -898,12 +1022,14 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         if (s == j.trig) trig_count = cnt;
         if (lane == 0) j.unit_counts[e * S + s] = cnt;
         if (chain && s != j.trig && ts.n > 0) {
-            for (int ti = lane; ti < ts.n; ti += 32)
-                if (w.alive[ti]) {
+            for (int ti = 0; ti < ts.n; ++ti)
+                if (w.alive[ti]) {  // warp-uniform
                     const float2 m = w.T[ti];
-                    if (!road(j, t, c, m.x, m.y)) w.alive[ti] = 0;
+                    const bool found = road_warp(j, t, c, m.x, m.y, lane);
+                    __syncwarp();
+                    if (lane == 0 && !found) w.alive[ti] = 0;
+                    __syncwarp();
                 }
-            __syncwarp();
         }
     }
     if (j.mode == 0 && lane < S && lane != j.trig) j.unit_counts[e * S + lane] = 0;
@@ -991,11 +1117,11 @@ __global__ void __launch_bounds__(128, 3) k_medium(const __grid_constant__ Job j
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     WarpTile<MediumCfg>& w = reinterpret_cast<WarpTile<MediumCfg>*>(smem_raw)[wi];
     const Cuts c{j.cx, j.cy, j.K};
-    const int n_med = *(volatile int32_t*)&j.ctrl->n_medium;
+    const int n_med = *(volatile int32_t*)&j.ctrl->n_medium, m0 = *(volatile int32_t*)&j.ctrl->m_begin;
     unsigned long long* ctr = &j.ctrl->work[EMIT ? 5 : 1];
     for (;;) {
         int gi = 0;
-        if (lane == 0) gi = (int)atomicAdd(ctr, 1ull);
+        if (lane == 0) gi = m0 + (int)atomicAdd(ctr, 1ull);
         gi = __shfl_sync(kFull, gi, 0);
         if (gi >= n_med) break;
         light_event<EMIT, MediumCfg>(j, w, lane, c, j.mlist[gi]);
@@ -1055,6 +1181,8 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
             } else if (st == 1) {
                 atomicOr(&j.ctrl->status, kStInvalid);
                 j.ev_class[e] = kClsInvalid;
+            } else if (gi < 0) {
+                j.ev_class[e] = kClsGeneric;  // one-launch form: the same block goes on unpruned
             } else {
                 heavy_to_generic(j, gi, e);
             }
@@ -1067,8 +1195,12 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
     }
     __syncthreads();
     int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
+    // the station's trigger-slope searches run on the warps beside its
+    // enumeration rounds (both only read the staged tile)
+    const bool empty = sm.meta[0].nlive == 0 || sm.meta[1].nlive == 0 || sm.meta[2].nlive == 0;
+    const RoadItems rd{T, alive, EMIT || empty ? 0 : nT};
     enum_station<EMIT, true>(j, HTile{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
-                       cnt_expected, u, &sm.s_rank, kClsHeavy, &sm.s_next);
+                       cnt_expected, u, &sm.s_rank, kClsHeavy, &sm.s_next, &rd);
     __syncthreads();
     cnt = sm.s_rank;
     if (EMIT) {
@@ -1076,14 +1208,8 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
         return true;
     }
     if (tid == 0) j.unit_counts[u] = cnt;
-    if (nT > 0) {
-        const HTile t{sm.P, sm.idx, sm.bst, sm.meta};
-        for (int ti = tid; ti < nT; ti += kHThreads)
-            if (alive[ti]) {
-                const float2 m = T[ti];
-                if (!road(j, t, c, m.x, m.y)) alive[ti] = 0;
-            }
-    }
+    if (empty)  // no triplet at all in this station: no slope finds one
+        for (int ti = tid; ti < nT; ti += kHThreads) alive[ti] = 0;
     return true;
 }
 
@@ -1173,7 +1299,9 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
 constexpr int kSortCap = 4096;
 __global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ Job j) {
     __shared__ unsigned long long key[kSortCap];  // hits << 32 | event
-    const int n = *(volatile int32_t*)&j.ctrl->n_heavy;
+    const int h0 = *(volatile int32_t*)&j.ctrl->h_begin;
+    const int n = *(volatile int32_t*)&j.ctrl->n_heavy - h0;
+    int32_t* list = j.hlist + h0;
     if (n < 2 || n > kSortCap) return;
     int m = 2;
     while (m < n) m <<= 1;
@@ -1181,7 +1309,7 @@ __global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ Job
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         unsigned long long k = 0;  // padding sorts last
         if (i < n) {
-            const int32_t e = j.hlist[i];
+            const int32_t e = list[i];
             const int64_t hits = j.off[(e + 1) * S3] - j.off[e * S3];
             k = ((unsigned long long)hits << 32) | (uint32_t)e;
         }
@@ -1203,7 +1331,7 @@ __global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ Job
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) j.hlist[i] = (int32_t)(uint32_t)key[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) list[i] = (int32_t)(uint32_t)key[i];
 }
 
 // Counting pass: persistent blocks take block-tile events from the list.
@@ -1211,9 +1339,9 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy(const __grid_constant__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem& sm = *reinterpret_cast<HeavySmem*>(smem_raw);
     const Cuts c{j.cx, j.cy, j.K};
-    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
+    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy, h0 = *(volatile int32_t*)&j.ctrl->h_begin;
     for (;;) {
-        if (threadIdx.x == 0) sm.s_gi = (int)atomicAdd(&j.ctrl->work[2], 1ull);
+        if (threadIdx.x == 0) sm.s_gi = h0 + (int)atomicAdd(&j.ctrl->work[2], 1ull);
         __syncthreads();
         const int gi = sm.s_gi;
         __syncthreads();
@@ -1234,7 +1362,8 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_const
     if (!EMIT && (j.mode != 1 || S < 2)) return;
     const int per = EMIT ? (j.mode == 1 ? S : 1) : S - 1;  // units per event
     const Cuts c{j.cx, j.cy, j.K};
-    const long long n_items = (long long)*(volatile int32_t*)&j.ctrl->n_heavy * per;
+    const int h0 = *(volatile int32_t*)&j.ctrl->h_begin;
+    const long long n_items = (long long)(*(volatile int32_t*)&j.ctrl->n_heavy - h0) * per;
     for (;;) {
         // thread 0 takes an item and decides (the state it reads may change
         // under other blocks; the block must act on one reading)
@@ -1242,7 +1371,7 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_const
             long long k = (long long)atomicAdd(&j.ctrl->work[EMIT ? 6 : 8], 1ull);
             int hx = 0, hy = 0;
             if (k < n_items) {
-                const int gi = (int)(k / per);
+                const int gi = h0 + (int)(k / per);
                 const int64_t e = j.hlist[gi];
                 const int s = station_of((int)(k % per) + (EMIT ? 0 : 1), j.trig);
                 bool skip = j.ev_class[e] != kClsHeavy;
@@ -1266,7 +1395,7 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_const
         __syncthreads();
         if (k >= n_items) break;
         if (k < 0) continue;
-        const int gi = (int)(k / per);
+        const int gi = h0 + (int)(k / per);
         const int64_t e = j.hlist[gi];
         const int s = station_of((int)(k % per) + (EMIT ? 0 : 1), j.trig);
         load_event_offsets(j, sm, e);
@@ -1281,10 +1410,10 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_const
 // the trigger slopes still alive after every station (one warp per event).
 __global__ void k_heavy_final(const __grid_constant__ Job j) {
     if (j.mode != 1 || j.S < 2) return;
-    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy;
+    const int n_heavy = *(volatile int32_t*)&j.ctrl->n_heavy, h0 = *(volatile int32_t*)&j.ctrl->h_begin;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < n_heavy; gi += nw) {
+    for (int gi = h0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); gi < n_heavy; gi += nw) {
         const int2 h = j.hT[gi];
         const int64_t e = j.hlist[gi];
         if (h.y < 0 || j.ev_class[e] != kClsHeavy) continue;
@@ -1338,124 +1467,266 @@ __device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, fl
     return true;
 }
 
+// Shared scratch of the unpruned search of one event (from the caller).
+struct GenShared {
+    int32_t* soff;  // [3 * kMaxStations + 1] the event's offsets
+    int* s_count;
+    int* s_cand;
+    int* s_bad;
+};
+
+// The unpruned search of one event by one block: any size, any coordinates
+// (pruning only where the per-hit bound is finite).  Counting pass: unit
+// counts, track count and recorded entries; emit pass: rows.  All threads of
+// the block call it.
+template <bool EMIT>
+__device__ void generic_event(const Job& j, int64_t e, const GenShared& g) {
+    const Cuts c{j.cx, j.cy, j.K};
+    const int S = j.S, S3 = 3 * S;
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    int32_t* soff = g.soff;
+    __syncthreads();  // earlier users of the shared scratch are done
+    for (int i = threadIdx.x; i <= S3; i += blockDim.x) soff[i] = j.off[e * S3 + i];
+    if (threadIdx.x == 0) *g.s_cand = 0;
+    __syncthreads();
+    int trig_count = 0;
+    bool bad_event = false;
+    for (int si = 0; si < nproc && !bad_event; ++si) {
+        const int s = station_of(si, j.trig);
+        const int64_t u = e * S + s;
+        const int32_t* o = soff + 3 * s;
+        if (EMIT && j.unit_counts[u] == 0) continue;
+        if (threadIdx.x == 0) {
+            *g.s_count = 0;
+            *g.s_bad = 0;
+        }
+        __syncthreads();
+        if (!EMIT) {
+            for (int32_t h = o[0] + threadIdx.x; h < o[3]; h += blockDim.x)
+                if (__ldg(j.z + h) <= 0.0f) *g.s_bad = 1;
+            __syncthreads();
+            if (*g.s_bad) {
+                if (threadIdx.x == 0) {
+                    atomicOr(&j.ctrl->status, kStInvalid);
+                    j.ev_class[e] = kClsInvalid;
+                }
+                bad_event = true;
+                break;
+            }
+        }
+        const int64_t n0 = o[1] - o[0], n1 = o[2] - o[1], n2 = o[3] - o[2];
+        const int64_t npairs = n0 * n1;
+        int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
+        const int ulimit = EMIT ? j.unit_counts[u] : 0;
+        int local = 0;
+        const bool collect = !EMIT && chain && s == j.trig;
+        for (int64_t p = threadIdx.x; p < npairs; p += blockDim.x) {
+            const int64_t i = p / n1, jx = p - i * n1;
+            const GHit hi = ghit(j, o[0] + i), hj = ghit(j, o[1] + jx);
+            if (!hi.p.live || !hj.p.live) continue;
+            if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hj.p.sx, hj.p.sy, __fadd_rn(hi.p.b, hj.p.b)))
+                continue;
+            for (int64_t k = 0; k < n2; ++k) {
+                const GHit hk = ghit(j, o[2] + k);
+                if (!hk.p.live) continue;
+                if (!hk.p.wild) {
+                    if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hi.p.b, hk.p.b)))
+                        continue;
+                    if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hj.p.b, hk.p.b)))
+                        continue;
+                }
+                const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
+                float mx, my;
+                if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
+                ++local;
+                if (!EMIT && j.tscr) {
+                    const int rk = atomicAdd(g.s_count, 1);
+                    if (i >= kPackLimit || jx >= kPackLimit || k >= kPackLimit) {
+                        atomicOr(&j.ctrl->status, kStNoScratch);
+                    } else {
+                        const unsigned long long b = atomicAdd(&j.ctrl->scratch_n, 1ull);
+                        if (b < (unsigned long long)j.tscr_cap) {
+                            TripEntry te;
+                            te.unit = (int32_t)u;
+                            te.rank = rk;
+                            te.ijk = (unsigned long long)i | ((unsigned long long)jx << 20) |
+                                     ((unsigned long long)k << 40) | ((unsigned long long)kClsGeneric << kTagShift);
+                            j.tscr[b] = te;
+                        }
+                    }
+                }
+                if (EMIT) {
+                    const int pos = atomicAdd(g.s_count, 1);
+                    if (pos < ulimit) {  // never past the unit's rows
+                        int32_t* r = rows + 3 * (int64_t)pos;
+                        r[0] = (int32_t)i;
+                        r[1] = (int32_t)jx;
+                        r[2] = (int32_t)k;
+                    }
+                }
+                if (collect && road_global(j, soff, c, mx, my)) atomicAdd(g.s_cand, 1);
+            }
+        }
+        if (!EMIT && !j.tscr && local) atomicAdd(g.s_count, local);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (EMIT) {
+                if (*g.s_count != j.unit_counts[u]) atomicOr(&j.ctrl->status, kStEmitMismatch);
+            } else {
+                j.unit_counts[u] = *g.s_count;
+            }
+        }
+        if (s == j.trig) trig_count = *g.s_count;
+        __syncthreads();
+    }
+    if (!EMIT && !bad_event && threadIdx.x == 0) {
+        if (j.mode == 0)
+            for (int s = 0; s < S; ++s)
+                if (s != j.trig) j.unit_counts[e * S + s] = 0;
+        j.track_counts[e] = chain ? *g.s_cand : trig_count;
+    }
+    __syncthreads();
+}
+
+// Persistent blocks take the events of the unpruned list.
 template <bool EMIT>
 __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ Job j) {
     __shared__ int32_t soff[3 * kMaxStations + 1];
     __shared__ int s_gi, s_count, s_cand, s_bad;
-    const Cuts c{j.cx, j.cy, j.K};
-    const int n_gen = *(volatile int32_t*)&j.ctrl->n_generic;
-    const int S = j.S, S3 = 3 * S;
-    const bool chain = j.mode == 1 && S > 1;
-    const int nproc = j.mode == 1 ? S : 1;
+    const int n_gen = *(volatile int32_t*)&j.ctrl->n_generic, g0 = *(volatile int32_t*)&j.ctrl->g_begin;
     for (;;) {
-        if (threadIdx.x == 0) s_gi = (int)atomicAdd(&j.ctrl->work[EMIT ? 7 : 3], 1ull);
+        if (threadIdx.x == 0) s_gi = g0 + (int)atomicAdd(&j.ctrl->work[EMIT ? 7 : 3], 1ull);
         __syncthreads();
         const int gi = s_gi;
         if (gi >= n_gen) break;
         const int64_t e = j.glist[gi];
-        for (int i = threadIdx.x; i <= S3; i += blockDim.x) soff[i] = j.off[e * S3 + i];
-        if (threadIdx.x == 0) s_cand = 0;
-        __syncthreads();
-        if (EMIT && j.ev_class[e] != kClsGeneric) continue;
-        int trig_count = 0;
-        bool bad_event = false;
-        for (int si = 0; si < nproc && !bad_event; ++si) {
-            const int s = station_of(si, j.trig);
-            const int64_t u = e * S + s;
-            const int32_t* o = soff + 3 * s;
-            if (EMIT && j.unit_counts[u] == 0) continue;
-            if (threadIdx.x == 0) {
-                s_count = 0;
-                s_bad = 0;
-            }
-            __syncthreads();
-            if (!EMIT) {
-                for (int32_t h = o[0] + threadIdx.x; h < o[3]; h += blockDim.x)
-                    if (__ldg(j.z + h) <= 0.0f) s_bad = 1;
-                __syncthreads();
-                if (s_bad) {
-                    if (threadIdx.x == 0) {
-                        atomicOr(&j.ctrl->status, kStInvalid);
-                        j.ev_class[e] = kClsInvalid;
-                    }
-                    bad_event = true;
-                    break;
-                }
-            }
-            const int64_t n0 = o[1] - o[0], n1 = o[2] - o[1], n2 = o[3] - o[2];
-            const int64_t npairs = n0 * n1;
-            int32_t* rows = EMIT ? j.triplets + 3 * j.trip_off[u] : nullptr;
-            const int ulimit = EMIT ? j.unit_counts[u] : 0;
-            int local = 0;
-            const bool collect = !EMIT && chain && s == j.trig;
-            for (int64_t p = threadIdx.x; p < npairs; p += blockDim.x) {
-                const int64_t i = p / n1, jx = p - i * n1;
-                const GHit hi = ghit(j, o[0] + i), hj = ghit(j, o[1] + jx);
-                if (!hi.p.live || !hj.p.live) continue;
-                if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hj.p.sx, hj.p.sy, __fadd_rn(hi.p.b, hj.p.b)))
-                    continue;
-                for (int64_t k = 0; k < n2; ++k) {
-                    const GHit hk = ghit(j, o[2] + k);
-                    if (!hk.p.live) continue;
-                    if (!hk.p.wild) {
-                        if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hi.p.b, hk.p.b)))
-                            continue;
-                        if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hj.p.b, hk.p.b)))
-                            continue;
-                    }
-                    const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
-                    float mx, my;
-                    if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
-                    ++local;
-                    if (!EMIT && j.tscr) {
-                        const int rk = atomicAdd(&s_count, 1);
-                        if (i >= kPackLimit || jx >= kPackLimit || k >= kPackLimit) {
-                            atomicOr(&j.ctrl->status, kStNoScratch);
-                        } else {
-                            const unsigned long long b = atomicAdd(&j.ctrl->scratch_n, 1ull);
-                            if (b < (unsigned long long)j.tscr_cap) {
-                                TripEntry te;
-                                te.unit = (int32_t)u;
-                                te.rank = rk;
-                                te.ijk = (unsigned long long)i | ((unsigned long long)jx << 20) |
-                                         ((unsigned long long)k << 40) |
-                                         ((unsigned long long)kClsGeneric << kTagShift);
-                                j.tscr[b] = te;
-                            }
-                        }
-                    }
-                    if (EMIT) {
-                        const int pos = atomicAdd(&s_count, 1);
-                        if (pos < ulimit) {  // never past the unit's rows
-                            int32_t* r = rows + 3 * (int64_t)pos;
-                            r[0] = (int32_t)i;
-                            r[1] = (int32_t)jx;
-                            r[2] = (int32_t)k;
-                        }
-                    }
-                    if (collect && road_global(j, soff, c, mx, my)) atomicAdd(&s_cand, 1);
-                }
-            }
-            if (!EMIT && !j.tscr && local) atomicAdd(&s_count, local);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (EMIT) {
-                    if (s_count != j.unit_counts[u]) atomicOr(&j.ctrl->status, kStEmitMismatch);
-                } else {
-                    j.unit_counts[u] = s_count;
-                }
-            }
-            if (s == j.trig) trig_count = s_count;
-            __syncthreads();
-        }
-        if (!EMIT && !bad_event && threadIdx.x == 0) {
-            if (j.mode == 0)
-                for (int s = 0; s < S; ++s)
-                    if (s != j.trig) j.unit_counts[e * S + s] = 0;
-            j.track_counts[e] = chain ? s_cand : trig_count;
-        }
+        if (!EMIT || j.ev_class[e] == kClsGeneric) generic_event<EMIT>(j, e, GenShared{soff, &s_count, &s_cand, &s_bad});
         __syncthreads();
     }
+}
+
+// ------------------------------------------------- one-launch form, blocks
+
+// The one-launch form (jpsi_run_plain) has no event lists, queues, sort,
+// pool hand-off or graphs: a static grid of one warp per event (k_light with
+// Job::plain), then a static grid of one block per event (below).  A block
+// whose event the warp finished returns at once; the others run the whole
+// event here: every station on the block tile, or the unpruned search when
+// the event does not fit the tile or has extreme coordinates.
+constexpr int kPlainTCap = 128;  // trigger slopes kept in shared memory (more: the pool)
+
+struct PlainSmem {
+    HeavySmem h;
+    float2 T[kPlainTCap];
+    uint8_t alive[kPlainTCap];
+};
+
+// One block-tile event of the one-launch form.  Returns true when the event
+// must go on to the unpruned search (its class is then kClsGeneric).
+template <bool EMIT>
+__device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
+    HeavySmem& sm = ps.h;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int S = j.S;
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    const Cuts c{j.cx, j.cy, j.K};
+    load_event_offsets(j, sm, e);
+    if (EMIT) {
+        for (int si = 0; si < nproc; ++si) {
+            const int s = station_of(si, j.trig);
+            if (j.unit_counts[e * S + s] == 0) continue;
+            TSink ts{false, nullptr, 0, nullptr, 0};
+            int cnt = 0;
+            heavy_unit<true>(j, sm, c, -1, e, s, ts, nullptr, nullptr, 0, cnt);
+            __syncthreads();
+        }
+        return false;
+    }
+    bool fits = true;
+    for (int si = 0; si < nproc; ++si) {
+        const int32_t* o = sm.off + 3 * station_of(si, j.trig);
+        if (o[1] - o[0] > kHLayerCap || o[2] - o[1] > kHLayerCap || o[3] - o[2] > kHLayerCap || o[3] - o[0] > kHHCap)
+            fits = false;
+    }
+    if (!fits) {
+        if (tid == 0) j.ev_class[e] = kClsGeneric;
+        return true;
+    }
+    float2* T = ps.T;
+    uint8_t* alive = ps.alive;
+    int trig_count = 0, nT = 0;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        if (tid == 0) sm.s_nT = 0;
+        __syncthreads();
+        TSink ts{chain && si == 0, T, kPlainTCap, &sm.s_nT, 0};
+        int cnt = 0;
+        if (!heavy_unit<false>(j, sm, c, -1, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) {
+            __syncthreads();
+            return j.ev_class[e] == kClsGeneric;
+        }
+        __syncthreads();
+        if (si > 0) continue;
+        trig_count = cnt;
+        if (!chain) break;
+        nT = sm.s_nT;
+        if (nT > kPlainTCap) {
+            // more slopes than the block keeps: room in the batch's pool, and
+            // the trigger station once more (same count, nothing recorded)
+            if (tid == 0) sm.s_pool = atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nT);
+            __syncthreads();
+            const unsigned long long pb = sm.s_pool;
+            if (pb + (unsigned long long)nT > (unsigned long long)j.tpool_cap) {
+                if (tid == 0) j.ev_class[e] = kClsGeneric;
+                return true;
+            }
+            T = j.tpool + pb;
+            alive = j.tpool_alive + pb;
+            if (tid == 0) sm.s_nT = 0;
+            __syncthreads();
+            TSink ts2{true, T, nT, &sm.s_nT, 0};
+            ts2.norec = true;
+            if (!heavy_unit<false>(j, sm, c, -1, e, s, ts2, nullptr, nullptr, 0, cnt)) {
+                __syncthreads();
+                return j.ev_class[e] == kClsGeneric;
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < nT; i += kHThreads) alive[i] = 1;
+        __syncthreads();
+    }
+    int tc = trig_count;
+    if (chain) {
+        if (tid == 0) sm.s_cand = 0;
+        __syncthreads();
+        int a = 0;
+        for (int ti = tid; ti < nT; ti += kHThreads) a += alive[ti];
+        a = __reduce_add_sync(kFull, a);
+        if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
+        __syncthreads();
+        tc = sm.s_cand;
+    }
+    if (tid == 0) {
+        if (j.mode == 0)
+            for (int s = 0; s < S; ++s)
+                if (s != j.trig) j.unit_counts[e * S + s] = 0;
+        j.track_counts[e] = tc;
+    }
+    return false;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(kHThreads, 3) k_plain_block(const __grid_constant__ Job j) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PlainSmem& ps = *reinterpret_cast<PlainSmem*>(smem_raw);
+    const int64_t e = j.ev_begin + blockIdx.x;
+    if (e >= j.ev_begin + j.ev_count) return;
+    const uint8_t cls = j.ev_class[e];
+    bool generic = cls == kClsGeneric;
+    if (cls == kClsHeavy) generic = plain_block_event<EMIT>(j, ps, e);
+    if (generic) generic_event<EMIT>(j, e, GenShared{ps.h.off, &ps.h.s_rank, &ps.h.s_cand, &ps.h.s_next});
 }
 
 // -------------------------------------------------------- accept bits
@@ -1620,14 +1891,23 @@ __global__ void __launch_bounds__(256) k_expand_z(const int32_t* __restrict__ of
 size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile<SmallCfg>); }
 static size_t medium_smem_bytes() { return (size_t)MediumCfg::WPB * sizeof(WarpTile<MediumCfg>); }
 size_t heavy_smem_bytes() { return sizeof(HeavySmem); }
+static size_t plain_smem_bytes() { return sizeof(PlainSmem); }
 
-static bool g_attr_done = false;
+// Kernel attributes are per device: set once for each device a context or a
+// call runs on (serving threads may get here at the same time).
+static std::mutex g_attr_mu;
+static uint64_t g_attr_done = 0;  // bit d: device d done (devices >= 64: every call)
 
 static cudaError_t ensure_attrs() {
-    if (g_attr_done) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+    if (g_attr_done & bit) return cudaSuccess;
     const int maxw = 8;
-    cudaError_t e = cudaFuncSetAttribute(k_light<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)light_smem_bytes(maxw));
+    e = cudaFuncSetAttribute(k_light<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)light_smem_bytes(maxw));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_light<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)light_smem_bytes(maxw));
@@ -1643,7 +1923,13 @@ static cudaError_t ensure_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_heavy_units<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)heavy_smem_bytes());
-    if (e == cudaSuccess) g_attr_done = true;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_plain_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plain_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_plain_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plain_smem_bytes());
+    if (e == cudaSuccess) g_attr_done |= bit;
     return e;
 }
 
@@ -1728,6 +2014,47 @@ cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, 
     return cudaGetLastError();
 }
 
+// One-launch form: the static warp grid, then the static block grid and the
+// tail (accept bits, scan); its emit phase is the same two grids.
+static cudaError_t launch_plain_grids(const Job& job, bool emit, bool warps, bool blocks, const LaunchCfg& lc,
+                                      cudaStream_t st) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    Job j = job;
+    j.persistent = 0;
+    j.plain = 1;
+    const int wpb = lc.light_wpb;
+    const int64_t n = j.ev_count;
+    if (warps) {
+        const int64_t nb = std::max<int64_t>((n + wpb - 1) / wpb, 1);
+        if (emit)
+            k_light<true><<<(unsigned)nb, wpb * 32, light_smem_bytes(wpb), st>>>(j);
+        else
+            k_light<false><<<(unsigned)nb, wpb * 32, light_smem_bytes(wpb), st>>>(j);
+    }
+    if (blocks) {
+        const unsigned nb = (unsigned)std::max<int64_t>(n, 1);
+        if (emit)
+            k_plain_block<true><<<nb, kHThreads, plain_smem_bytes(), st>>>(j);
+        else
+            k_plain_block<false><<<nb, kHThreads, plain_smem_bytes(), st>>>(j);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_light(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    return launch_plain_grids(j, false, true, false, lc, st);
+}
+
+cudaError_t launch_plain_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    const cudaError_t e = launch_plain_grids(j, false, false, true, lc, st);
+    return e != cudaSuccess ? e : launch_count_tail(j, lc, st);
+}
+
+cudaError_t launch_plain_emit(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
+    return launch_plain_grids(j, true, true, true, lc, st);
+}
+
 cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
     k_scatter<<<lc.scan_blocks, 256, 0, st>>>(j);
     return cudaGetLastError();
@@ -1801,7 +2128,6 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
         p->ndf < 1 || p->min_candidates < 0 || !(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) ||
         std::isinf(p->t_xz) || std::isinf(p->t_yz))
         return JPSI_EINVAL;
-    const int64_t S = p->n_stations;
     if (b->n_events < 0 || b->n_events > kNoAllocMaxEvents) return JPSI_EINVAL;  // beyond the static scratch
     if (b->n_hits < 0 || b->n_hits >= ((int64_t)1 << 31) || (b->n_events == 0 && b->n_hits != 0)) return JPSI_EINVAL;
     if (b->n_events == 0) return JPSI_OK;
@@ -1834,6 +2160,8 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
         j.K = f;
     }
     j.grab = 2;
+    j.cap_small = SmallCfg::LAYER_CAP;
+    j.cap_medium = MediumCfg::LAYER_CAP;
     j.persistent = 1;
     j.unit_counts = unit_counts;
     j.track_counts = track_counts;
@@ -1843,7 +2171,6 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     j.hlist = lists + kNoAllocMaxEvents;
     j.glist = lists + 2 * kNoAllocMaxEvents;
     j.ctrl = dctrl;  // tlist, accept bits, offsets, triplets and entries stay null: the warp kernel alone runs
-    (void)S;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int n_sm = 0;
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return JPSI_ECUDA;

@@ -431,3 +431,20 @@ def test_geometry_z_table_host(lib, synth_mod, n):
     # no z and no table: refused
     hb = lib.make_batch(b["x"], b["y"], None, b["offsets"], n, b["n_hits"])
     assert lib.jpsi_run_host(ctx.ctx, hb, o, 0) == lib.JPSI_EINVAL
+
+
+@pytest.mark.parametrize("ndf,minc,cuts", [(3, 2, (0.03, 0.025)), (3, 2, (0.25, 0.25)), (2, 1, (0.25, 0.25)),
+                                           (2, 3, (0.25, 0.25)), (3, 0, (0.25, 0.25))])
+def test_ndf_and_min_candidates(lib, oracle_mod, synth_mod, ndf, minc, cuts):
+    # the degrees of freedom scale the cut (C = fl32(ndf * t)) and
+    # min_candidates sets the accept threshold (Sec. 3.2 steps 2b and 3);
+    # the paper's printed cuts are tried with ndf = 3 as well
+    for wl, n in (("poisson20_1k", 1000), ("poisson100_1m", 3000)):
+        b = synth_mod.generate(wl, 0, n)
+        for mode in (0, 1):
+            ref = oracle_mod.run(oracle_mod.params(4, mode, t_xz=cuts[0], t_yz=cuts[1], ndf=ndf, min_candidates=minc),
+                                 b, n_threads=16)
+            ctx = lib.Context(lib.params(4, mode, t_xz=cuts[0], t_yz=cuts[1], ndf=ndf, min_candidates=minc))
+            for form in ("plain", "batched"):
+                assert_same(gpu_select(ctx, b, form=form), ref, n * 4, label=f"{wl} mode={mode} {form}")
+            ctx.close()

@@ -358,3 +358,30 @@ def test_fp64_audit_agrees_away_from_cut(oracle_mod, synth_mod):
     c = {tuple(v) for v in _canon(r64, 1200)}
     # flips are only possible within a relative 1e-5 of the cut; none expected here
     assert len(a ^ c) <= 2
+
+
+def test_ndf_scales_the_cut(oracle_mod):
+    # "MSD per dof <= t" is S <= fl32(ndf * t).  x = (1, 2, 4) at z = (1, 2, 3)
+    # has S* = 5/14 = 0.357...: above 2 * 0.15 = 0.3, below 3 * 0.15 = 0.45
+    assert oracle_mod.cut(3, 0.15) == np.float32(np.float32(3.0) * np.float32(0.15))
+    ev = [[(1.0, 0.0, 1.0)], [(2.0, 0.0, 2.0)], [(4.0, 0.0, 3.0)]]
+    b = make_batch([ev], 1)
+    for ndf, passes in ((2, False), (3, True), (1, False)):
+        r = oracle_mod.run(oracle_mod.params(1, 0, t_xz=0.15, ndf=ndf, min_candidates=1), b)
+        assert r["status"] == 0 and int(r["unit_counts"][0]) == int(passes), ndf
+        assert bool(accept_list(r["accept_bits"], 1)[0]) == passes
+
+
+def test_min_candidates_threshold(oracle_mod):
+    # exactly two passing triplets (two straight tracks, no other hits that
+    # combine): accepted for min_candidates 0, 1, 2, rejected for 3; 0 accepts
+    # an event without any triplet too
+    z = [120.0, 130.0, 140.0]
+    tracks = [(0.1, 0.2), (-0.25, 0.05)]
+    ev = [[(tx * zz, ty * zz, zz) for tx, ty in tracks] for zz in z]
+    empty = [[], [], []]
+    b = make_batch([ev, empty], 1)
+    for minc, acc in ((0, [True, True]), (1, [True, False]), (2, [True, False]), (3, [False, False])):
+        r = oracle_mod.run(oracle_mod.params(1, 0, t_xz=0.01, min_candidates=minc), b)
+        assert r["status"] == 0 and list(r["track_counts"]) == [2, 0]
+        assert list(accept_list(r["accept_bits"], 2)) == acc, minc
