@@ -70,16 +70,28 @@ struct WCfg {
     static constexpr int WPB = WPB_;                // warps per block (medium: fixed)
 };
 using SmallCfg = WCfg<6, 384, 64, 1, kClsLight, 0>;      // 192 hits/layer, 384/station
+// the size limits of the medium tile (a 2-warp block tile, MedBCfg below)
 using MediumCfg = WCfg<12, 960, 32, 16, kClsMedium, 4>;  // 384 hits/layer, 960/station
 
-// block-tile path
-constexpr int kHThreads = 256;
-constexpr int kHWarps = kHThreads / 32;
-constexpr int kHRMax = 8;                         // hits per thread per layer
-constexpr int kHLayerCap = kHThreads * kHRMax;    // 2048 hits per layer
-constexpr int kHHCap = 5632;                      // hits per station tile
-constexpr int kNXH = 64, kNYH = 32;               // slope bins per layer in s_x, s_y
-constexpr int kNCH = kNXH * kNYH;                 // cells per layer
+// block-tile paths: a block of THREADS threads stages a station (each thread
+// up to RMAX hits per layer) into NY x NX cells per layer, and its warps
+// share the station's enumeration rounds and trigger-slope searches
+template <int THREADS_, int RMAX_, int HCAP_, int NX_, int NY_, uint8_t CLS_>
+struct BCfg {
+    static constexpr int THREADS = THREADS_, WARPS = THREADS_ / 32;
+    static constexpr int RMAX = RMAX_;                   // hits per thread per layer
+    static constexpr int LAYER_CAP = THREADS_ * RMAX_;   // hits per layer
+    static constexpr int HCAP = HCAP_;                   // hits per station tile
+    static constexpr int NX = NX_, NY = NY_, NC = NX_ * NY_;
+    static constexpr uint8_t CLS = CLS_;                 // event class of this path
+};
+// the block tile proper: 8 warps, 2048 hits per layer, 5632 per station, 32 x 64 cells
+using HeavyCfg = BCfg<256, 8, 5632, 64, 32, kClsHeavy>;
+// the medium tile: 2 warps, 384 hits per layer, 960 per station, 16 x 32 cells
+using MedBCfg = BCfg<64, 6, 960, 32, 16, kClsMedium>;
+constexpr int kHThreads = HeavyCfg::THREADS;
+constexpr int kHLayerCap = HeavyCfg::LAYER_CAP;
+constexpr int kHHCap = HeavyCfg::HCAP;
 
 struct LayerMeta {
     float lox, scx, loy, scy;  // cell map: column = bin of s_x, row = bin of s_y
@@ -99,7 +111,6 @@ struct TileView {
     uint16_t* bst;  // [3 * NC + 1] tile positions: layer l, cell k at l * NC + k
     LayerMeta* meta;
 };
-using HTile = TileView<kNXH, kNYH>;
 
 template <class Cfg>
 struct WarpTile {
@@ -112,20 +123,22 @@ struct WarpTile {
     LayerMeta meta[3];
 };
 
-struct HeavySmem {
-    float2 P[kHHCap];
-    uint16_t idx[kHHCap];
-    uint32_t queue[kHWarps][kQCap];
-    alignas(4) uint16_t bst[3 * kNCH + 1];  // cell starts (cell counts while a layer is staged)
+template <class B>
+struct BlockSmem {
+    float2 P[B::HCAP];
+    uint16_t idx[B::HCAP];
+    uint32_t queue[B::WARPS][kQCap];
+    alignas(4) uint16_t bst[3 * B::NC + 1];  // cell starts (cell counts while a layer is staged)
     LayerMeta meta[3];
     int32_t off[3 * kMaxStations + 1];
-    int32_t wsum[kHWarps];
-    int red_i[kHWarps][2];
-    float red_f[kHWarps][5];
+    int32_t wsum[B::WARPS];
+    int red_i[B::WARPS][2];
+    float red_f[B::WARPS][5];
     unsigned long long s_pool;
     long long s_item;
     int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy, s_next;
 };
+using HeavySmem = BlockSmem<HeavyCfg>;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -365,30 +378,30 @@ __device__ int stage_station_warp(const Job& j, WarpTile<Cfg>& w, int lane, cons
 
 // ------------------------------------------------------ block staging
 
-// Block version of the staging for the block-tile path (256 threads, two
-// cells per thread).
-__device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t base, int32_t n, int32_t pbase,
+// Block version of the staging (block-tile paths).
+template <class B>
+__device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t base, int32_t n, int32_t pbase,
                                  int& nlive) {
-    constexpr int CPT = kNCH / kHThreads;  // cells per thread
-    static_assert(kNCH % kHThreads == 0, "cells per layer");
+    constexpr int CPT = B::NC / B::THREADS;  // cells per thread
+    static_assert(B::NC % B::THREADS == 0, "cells per layer");
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    float sx[kHRMax], sy[kHRMax];
-    int key[kHRMax];  // cell << 16 | rank in the cell once binned; -1: not stored
+    float sx[B::RMAX], sy[B::RMAX];
+    int key[B::RMAX];  // cell << 16 | rank in the cell once binned; -1: not stored
     static_assert(CPT % 2 == 0, "two 16-bit cell counters per word");
     float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
     bool zbad = false, wild = false;
-    uint16_t* bst = sm.bst + l * kNCH;  // the end of layer l is the start of layer l + 1
+    uint16_t* bst = sm.bst + l * B::NC;  // the end of layer l is the start of layer l + 1
 #pragma unroll
     for (int q = 0; q < CPT / 2; ++q) reinterpret_cast<uint32_t*>(bst)[CPT / 2 * tid + q] = 0;
 #pragma unroll
-    for (int r = 0; r < kHRMax; ++r) {
+    for (int r = 0; r < B::RMAX; ++r) {
         key[r] = -1;
         sx[r] = sy[r] = 0.0f;
     }
 #pragma unroll
-    for (int r = 0; r < kHRMax; ++r) {
-        if (kHThreads * r >= n) break;  // block-uniform
-        const int h = tid + kHThreads * r;
+    for (int r = 0; r < B::RMAX; ++r) {
+        if (B::THREADS * r >= n) break;  // block-uniform
+        const int h = tid + B::THREADS * r;
         const bool in = h < n;
         const int hc = in ? h : n - 1;
         const HitPrep p = hit_prep(__ldg(j.x + base + hc), __ldg(j.y + base + hc), __ldg(j.z + base + hc), j.K);
@@ -422,7 +435,7 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     __syncthreads();
     int anyz = 0, anyw = 0;
 #pragma unroll
-    for (int q = 0; q < kHWarps; ++q) {
+    for (int q = 0; q < B::WARPS; ++q) {
         lox = fminf(lox, sm.red_f[q][0]);
         hix = fmaxf(hix, sm.red_f[q][1]);
         loy = fminf(loy, sm.red_f[q][2]);
@@ -434,12 +447,12 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     __syncthreads();
     if (anyz) return 1;
     if (anyw) return 2;
-    const float scx = bin_scale(lox, hix, kNXH), scy = bin_scale(loy, hiy, kNYH);
+    const float scx = bin_scale(lox, hix, B::NX), scy = bin_scale(loy, hiy, B::NY);
 #pragma unroll
-    for (int r = 0; r < kHRMax; ++r) {
-        if (kHThreads * r >= n) break;
+    for (int r = 0; r < B::RMAX; ++r) {
+        if (B::THREADS * r >= n) break;
         if (key[r] >= 0) {
-            const int cell = slope_bin<kNYH>(sy[r], loy, scy) * kNXH + slope_bin<kNXH>(sx[r], lox, scx);
+            const int cell = slope_bin<B::NY>(sy[r], loy, scy) * B::NX + slope_bin<B::NX>(sx[r], lox, scx);
             key[r] = (cell << 16) | cell_count_add(bst, cell);
         }
     }
@@ -457,7 +470,7 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
     __syncthreads();
     int woff = 0, total = 0;
 #pragma unroll
-    for (int q = 0; q < kHWarps; ++q) {
+    for (int q = 0; q < B::WARPS; ++q) {
         woff += q < wp ? sm.wsum[q] : 0;
         total += sm.wsum[q];
     }
@@ -467,15 +480,15 @@ __device__ int stage_layer_block(const Job& j, HeavySmem& sm, int l, int32_t bas
         bst[CPT * tid + q] = (uint16_t)run;
         run += cs[q];
     }
-    if (tid == kHThreads - 1) bst[kNCH] = (uint16_t)(pbase + total);
+    if (tid == B::THREADS - 1) bst[B::NC] = (uint16_t)(pbase + total);
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kHRMax; ++r) {
-        if (kHThreads * r >= n) break;
+    for (int r = 0; r < B::RMAX; ++r) {
+        if (B::THREADS * r >= n) break;
         if (key[r] >= 0) {
             const int pos = bst[key[r] >> 16] + (key[r] & 0xffff);
             sm.P[pos] = make_float2(sx[r], sy[r]);
-            sm.idx[pos] = (uint16_t)(tid + kHThreads * r);
+            sm.idx[pos] = (uint16_t)(tid + B::THREADS * r);
         }
     }
     if (tid == 0) {
@@ -1022,14 +1035,14 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         if (s == j.trig) trig_count = cnt;
         if (lane == 0) j.unit_counts[e * S + s] = cnt;
         if (chain && s != j.trig && ts.n > 0) {
-            for (int ti = 0; ti < ts.n; ++ti)
-                if (w.alive[ti]) {  // warp-uniform
+            // one trigger slope per lane (a warp tile holds few; measured
+            // faster here than the warp-cooperative search of the block tile)
+            for (int ti = lane; ti < ts.n; ti += 32)
+                if (w.alive[ti]) {
                     const float2 m = w.T[ti];
-                    const bool found = road_warp(j, t, c, m.x, m.y, lane);
-                    __syncwarp();
-                    if (lane == 0 && !found) w.alive[ti] = 0;
-                    __syncwarp();
+                    if (!road(j, t, c, m.x, m.y)) w.alive[ti] = 0;
                 }
+            __syncwarp();
         }
     }
     if (j.mode == 0 && lane < S && lane != j.trig) j.unit_counts[e * S + lane] = 0;
@@ -1109,30 +1122,12 @@ __global__ void __maxnreg__(56) k_light(const __grid_constant__ Job j) {
     }
 }
 
-// Medium warp tiles: the events the small tiles passed on, one at a time per
-// warp from the medium list.
-template <bool EMIT>
-__global__ void __launch_bounds__(128, 3) k_medium(const __grid_constant__ Job j) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    WarpTile<MediumCfg>& w = reinterpret_cast<WarpTile<MediumCfg>*>(smem_raw)[wi];
-    const Cuts c{j.cx, j.cy, j.K};
-    const int n_med = *(volatile int32_t*)&j.ctrl->n_medium, m0 = *(volatile int32_t*)&j.ctrl->m_begin;
-    unsigned long long* ctr = &j.ctrl->work[EMIT ? 5 : 1];
-    for (;;) {
-        int gi = 0;
-        if (lane == 0) gi = m0 + (int)atomicAdd(ctr, 1ull);
-        gi = __shfl_sync(kFull, gi, 0);
-        if (gi >= n_med) break;
-        light_event<EMIT, MediumCfg>(j, w, lane, c, j.mlist[gi]);
-    }
-}
-
 // ------------------------------------------------------ block-tile path
 
 // Stages station s of the event whose offsets are in sm.off.  Returns 0, 1
 // (z <= 0) or 2 (not prunable).
-__device__ int stage_station_block(const Job& j, HeavySmem& sm, int s) {
+template <class B>
+__device__ int stage_station_block(const Job& j, BlockSmem<B>& sm, int s) {
     int pbase = 0;
     for (int l = 0; l < 3; ++l) {
         const int32_t b = sm.off[3 * s + l], e = sm.off[3 * s + l + 1];
@@ -1144,9 +1139,10 @@ __device__ int stage_station_block(const Job& j, HeavySmem& sm, int s) {
     return 0;
 }
 
-__device__ __forceinline__ void load_event_offsets(const Job& j, HeavySmem& sm, int64_t e) {
+template <class B>
+__device__ __forceinline__ void load_event_offsets(const Job& j, BlockSmem<B>& sm, int64_t e) {
     const int S3 = 3 * j.S;
-    for (int i = threadIdx.x; i <= S3; i += kHThreads) sm.off[i] = j.off[e * S3 + i];
+    for (int i = threadIdx.x; i <= S3; i += B::THREADS) sm.off[i] = j.off[e * S3 + i];
     __syncthreads();
 }
 
@@ -1167,9 +1163,15 @@ __device__ __forceinline__ void heavy_to_generic(const Job& j, int gi, int64_t e
 // Counting pass: writes the unit count (also returned in cnt); returns false
 // when the event left the path (then nothing else may be done for it).
 // Emit pass: writes rows.  Block-uniform arguments; all threads call it.
-template <bool EMIT>
-__device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, int64_t e, int s, TSink& ts,
+// Who hands an event on when a station cannot be pruned: gi >= 0 is the
+// event's block-tile list entry (its state in Job::hT);
+constexpr int kGiPlain = -1;  // the one-launch form: the same block goes on unpruned
+constexpr int kGiOwn = -2;    // a block that owns the whole event: to the unpruned list
+
+template <bool EMIT, class B>
+__device__ bool heavy_unit(const Job& j, BlockSmem<B>& sm, const Cuts& c, int gi, int64_t e, int s, TSink& ts,
                            const float2* T, uint8_t* alive, int nT, int& cnt) {
+    using TV = TileView<B::NX, B::NY>;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t u = e * j.S + s;
     const int cnt_expected = EMIT ? j.unit_counts[u] : 0;
@@ -1181,8 +1183,10 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
             } else if (st == 1) {
                 atomicOr(&j.ctrl->status, kStInvalid);
                 j.ev_class[e] = kClsInvalid;
-            } else if (gi < 0) {
-                j.ev_class[e] = kClsGeneric;  // one-launch form: the same block goes on unpruned
+            } else if (gi == kGiPlain) {
+                j.ev_class[e] = kClsGeneric;
+            } else if (gi == kGiOwn) {
+                push_event(j, e, kClsGeneric);
             } else {
                 heavy_to_generic(j, gi, e);
             }
@@ -1199,8 +1203,8 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
     // enumeration rounds (both only read the staged tile)
     const bool empty = sm.meta[0].nlive == 0 || sm.meta[1].nlive == 0 || sm.meta[2].nlive == 0;
     const RoadItems rd{T, alive, EMIT || empty ? 0 : nT};
-    enum_station<EMIT, true>(j, HTile{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
-                       cnt_expected, u, &sm.s_rank, kClsHeavy, &sm.s_next, &rd);
+    enum_station<EMIT, true>(j, TV{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
+                       cnt_expected, u, &sm.s_rank, B::CLS, &sm.s_next, &rd);
     __syncthreads();
     cnt = sm.s_rank;
     if (EMIT) {
@@ -1209,7 +1213,7 @@ __device__ bool heavy_unit(const Job& j, HeavySmem& sm, const Cuts& c, int gi, i
     }
     if (tid == 0) j.unit_counts[u] = cnt;
     if (empty)  // no triplet at all in this station: no slope finds one
-        for (int ti = tid; ti < nT; ti += kHThreads) alive[ti] = 0;
+        for (int ti = tid; ti < nT; ti += B::THREADS) alive[ti] = 0;
     return true;
 }
 
@@ -1289,6 +1293,95 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
             for (int s = 0; s < S; ++s)
                 if (s != j.trig) j.unit_counts[e * S + s] = 0;
         j.track_counts[e] = tc;
+    }
+}
+
+// Medium tile: 2-warp blocks take the events of the medium list, one at a
+// time, and run every station of their event: the trigger station first (in
+// CHAIN mode its passing triplets' slopes, at most kTCap, stay in shared
+// memory), then the others, whose enumeration rounds share the warps with
+// the searches for those slopes.  An event with more trigger slopes goes on
+// to the block tile; one with extreme coordinates to the unpruned kernel.
+struct MediumSmem {
+    BlockSmem<MedBCfg> b;
+    float2 T[kTCap];
+    uint8_t alive[kTCap];
+};
+
+template <bool EMIT>
+__device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_t e) {
+    BlockSmem<MedBCfg>& sm = ms.b;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int S = j.S;
+    const bool chain = j.mode == 1 && S > 1;
+    const int nproc = j.mode == 1 ? S : 1;
+    load_event_offsets(j, sm, e);
+    if (EMIT) {
+        for (int si = 0; si < nproc; ++si) {
+            const int s = station_of(si, j.trig);
+            if (j.unit_counts[e * S + s] == 0) continue;
+            TSink ts{false, nullptr, 0, nullptr, 0};
+            int cnt = 0;
+            heavy_unit<true>(j, sm, c, kGiOwn, e, s, ts, nullptr, nullptr, 0, cnt);
+            __syncthreads();
+        }
+        return;
+    }
+    int trig_count = 0, nT = 0;
+    for (int si = 0; si < nproc; ++si) {
+        const int s = station_of(si, j.trig);
+        if (tid == 0) sm.s_nT = 0;
+        __syncthreads();
+        TSink ts{chain && si == 0, ms.T, kTCap, &sm.s_nT, 0};
+        int cnt = 0;
+        if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt)) return;
+        __syncthreads();
+        if (si > 0) continue;
+        trig_count = cnt;
+        if (!chain) break;
+        nT = sm.s_nT;
+        if (nT > kTCap) {  // more trigger slopes than this tile keeps
+            if (tid == 0) push_event(j, e, kClsHeavy);
+            return;
+        }
+        for (int i = tid; i < nT; i += MedBCfg::THREADS) ms.alive[i] = 1;
+        __syncthreads();
+    }
+    int tc = trig_count;
+    if (chain) {
+        if (tid == 0) sm.s_cand = 0;
+        __syncthreads();
+        int a = 0;
+        for (int ti = tid; ti < nT; ti += MedBCfg::THREADS) a += ms.alive[ti];
+        a = __reduce_add_sync(kFull, a);
+        if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
+        __syncthreads();
+        tc = sm.s_cand;
+    }
+    if (tid == 0) {
+        if (j.mode == 0)
+            for (int s = 0; s < S; ++s)
+                if (s != j.trig) j.unit_counts[e * S + s] = 0;
+        j.track_counts[e] = tc;
+    }
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(MedBCfg::THREADS, 14) k_medium(const __grid_constant__ Job j) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MediumSmem& ms = *reinterpret_cast<MediumSmem*>(smem_raw);
+    const Cuts c{j.cx, j.cy, j.K};
+    const int n_med = *(volatile int32_t*)&j.ctrl->n_medium, m0 = *(volatile int32_t*)&j.ctrl->m_begin;
+    unsigned long long* ctr = &j.ctrl->work[EMIT ? 5 : 1];
+    for (;;) {
+        if (threadIdx.x == 0) ms.b.s_gi = m0 + (int)atomicAdd(ctr, 1ull);
+        __syncthreads();
+        const int gi = ms.b.s_gi;
+        __syncthreads();
+        if (gi >= n_med) break;
+        const int64_t e = j.mlist[gi];
+        if (!EMIT || j.ev_class[e] == kClsMedium) medium_event<EMIT>(j, ms, c, e);
+        __syncthreads();
     }
 }
 
@@ -1639,7 +1732,7 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
             if (j.unit_counts[e * S + s] == 0) continue;
             TSink ts{false, nullptr, 0, nullptr, 0};
             int cnt = 0;
-            heavy_unit<true>(j, sm, c, -1, e, s, ts, nullptr, nullptr, 0, cnt);
+            heavy_unit<true>(j, sm, c, kGiPlain, e, s, ts, nullptr, nullptr, 0, cnt);
             __syncthreads();
         }
         return false;
@@ -1663,7 +1756,7 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         __syncthreads();
         TSink ts{chain && si == 0, T, kPlainTCap, &sm.s_nT, 0};
         int cnt = 0;
-        if (!heavy_unit<false>(j, sm, c, -1, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) {
+        if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) {
             __syncthreads();
             return j.ev_class[e] == kClsGeneric;
         }
@@ -1688,7 +1781,7 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
             __syncthreads();
             TSink ts2{true, T, nT, &sm.s_nT, 0};
             ts2.norec = true;
-            if (!heavy_unit<false>(j, sm, c, -1, e, s, ts2, nullptr, nullptr, 0, cnt)) {
+            if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts2, nullptr, nullptr, 0, cnt)) {
                 __syncthreads();
                 return j.ev_class[e] == kClsGeneric;
             }
@@ -1889,7 +1982,7 @@ __global__ void __launch_bounds__(256) k_expand_z(const int32_t* __restrict__ of
 // ------------------------------------------------------------ launchers
 
 size_t light_smem_bytes(int wpb) { return (size_t)wpb * sizeof(WarpTile<SmallCfg>); }
-static size_t medium_smem_bytes() { return (size_t)MediumCfg::WPB * sizeof(WarpTile<MediumCfg>); }
+static size_t medium_smem_bytes() { return sizeof(MediumSmem); }
 size_t heavy_smem_bytes() { return sizeof(HeavySmem); }
 static size_t plain_smem_bytes() { return sizeof(PlainSmem); }
 
@@ -1954,7 +2047,7 @@ int heavy_max_blocks_per_sm() {
 int medium_max_blocks_per_sm() {
     if (ensure_attrs() != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_medium<false>, 32 * MediumCfg::WPB, medium_smem_bytes()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_medium<false>, MedBCfg::THREADS, medium_smem_bytes()) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1984,7 +2077,7 @@ cudaError_t launch_light_count(const Job& job, int64_t n_events, const LaunchCfg
 }
 
 cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st) {
-    k_medium<false><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
+    k_medium<false><<<lc.medium_blocks, MedBCfg::THREADS, medium_smem_bytes(), st>>>(j);
     k_sort_heavy<<<1, 1024, 0, st>>>(j);
     k_heavy<<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_heavy_units<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
@@ -2070,7 +2163,7 @@ cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg&
     j.persistent = persistent ? 1 : 0;
     const int64_t nb = persistent ? lc.light_blocks : std::max<int64_t>((n_events + wpb - 1) / wpb, 1);
     k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(j);
-    k_medium<true><<<lc.medium_blocks, 32 * MediumCfg::WPB, medium_smem_bytes(), st>>>(j);
+    k_medium<true><<<lc.medium_blocks, MedBCfg::THREADS, medium_smem_bytes(), st>>>(j);
     k_heavy_units<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
     return cudaGetLastError();
