@@ -444,7 +444,8 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         anyz |= sm.red_i[q][0];
         anyw |= sm.red_i[q][1];
     }
-    __syncthreads();
+    // (red_f / red_i are written again only in the next layer, behind the
+    // three barriers below)
     if (anyz) return 1;
     if (anyw) return 2;
     const float scx = bin_scale(lox, hix, B::NX), scy = bin_scale(loy, hiy, B::NY);
@@ -503,7 +504,8 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         m.nlive = total;
         sm.meta[l] = m;
     }
-    __syncthreads();
+    // no barrier here: the next layer works on its own cells and tile
+    // positions, and the caller synchronises before the tile is read
     nlive = total;
     return 0;
 }
@@ -594,17 +596,103 @@ __device__ __forceinline__ int runs_pos(const Runs& r, int o, int it) {
     return it < sp ? pa : pb;
 }
 
+// Position of the k-th (0-based) set bit of m (binary lifting over the
+// counts of lower bits; k < popc(m)).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1)
+        if (__popc(m & ((1u << (pos + s)) - 1u)) <= k) pos += s;
+    return pos;
+}
+
+// Triples that passed both pair tests and wait for their exact fit (block
+// paths): lane l < m holds one, as tile positions i | j << 16 and k.  The
+// fits (and the global loads of their hits) then run 32 at a time.
+struct Pending {
+    uint32_t pair = 0;
+    int k = 0;
+    int m = 0;
+};
+
+// P1 on the triples of the lanes with `has` (tile positions pi, pj, pk) and
+// what follows from a pass: the triplet's rank in its unit (warp-local on
+// the warp path, from a block-shared counter on the block path), its row
+// (emit pass), its slopes for the trigger sink (CHAIN) and its entry in the
+// scatter record.  All lanes call it.
+template <bool EMIT, class TV>
+__device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int lane, const Cuts& c, bool has, int pi,
+                                               int pj, int pk, TSink& ts, int32_t* rows, int limit, int64_t unit,
+                                               int* sh_rank, int tag, int& count) {
+    bool ok = false;
+    float mx = 0.f, my = 0.f;
+    int ii = 0, jj = 0, kk = 0;
+    if (has) {
+        const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
+        ii = t.idx[pi];
+        jj = t.idx[pj];
+        kk = t.idx[pk];
+        const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
+        const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
+        const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
+        ok = fit_pass(xs, ys, zs, c, mx, my);
+    }
+    const unsigned mask = __ballot_sync(kFull, ok);
+    if (mask) {
+        const int rk = __popc(mask & lanemask_lt()), np = __popc(mask);
+        int base = count;
+        if (sh_rank) {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(sh_rank, np);
+            base = __shfl_sync(kFull, b, 0);
+        }
+        if (EMIT && ok && base + rk < limit) {  // never past the unit's rows
+            int32_t* r = rows + 3 * (int64_t)(base + rk);
+            r[0] = ii;
+            r[1] = jj;
+            r[2] = kk;
+        }
+        if (ts.on) {
+            int tb = ts.n;
+            if (ts.sh_n) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(ts.sh_n, np);
+                tb = __shfl_sync(kFull, b, 0);
+            } else {
+                ts.n += np;
+            }
+            if (ok && tb + rk < ts.cap) ts.T[tb + rk] = make_float2(mx, my);
+        }
+        if (!EMIT && j.tscr && !ts.norec) {  // record for the scatter pass
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)np);
+            b = __shfl_sync(kFull, b, 0) + rk;
+            if (ok && b < (unsigned long long)j.tscr_cap) {
+                TripEntry te;
+                te.unit = (int32_t)unit;
+                te.rank = base + rk;
+                te.ijk = (unsigned long long)ii | ((unsigned long long)jj << 20) | ((unsigned long long)kk << 40) |
+                         ((unsigned long long)tag << kTagShift);
+                j.tscr[b] = te;
+            }
+        }
+        count += np;
+    }
+}
+
 // Drains a pair queue: every (i, j) against the L2 hits in the meet of both
 // cell windows.  The (pair, k) items of up to 32 pairs are spread evenly over
 // the lanes (a warp prefix sum over the window sizes; each lane finds the
-// pair owning its item by binary lifting).  Passing triplets get a rank
-// inside their unit: warp-local on the warp path, from a block-shared counter
-// on the block path.
-template <bool EMIT, class TV>
+// pair owning its item by binary lifting).  Items that pass both pair tests
+// get the exact fit at once (COMPACT false: the warp tile, where a station
+// has about one such item) or join the pending triples of `pd` first
+// (COMPACT true: the block paths), so that the global loads of the fits
+// run for 32 triples at a time.
+template <bool EMIT, bool COMPACT, class TV>
 __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
-                      TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count) {
+                      TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count,
+                      Pending& pd) {
     const float B02 = __fadd_rn(t.meta[0].bmax, t.meta[2].bmax), B12 = __fadd_rn(t.meta[1].bmax, t.meta[2].bmax);
-    const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int q = q0 + lane;
         uint32_t en = 0;
@@ -622,65 +710,48 @@ __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane
             const int o = owner_lane(rr.excl, it);
             const uint32_t eo = __shfl_sync(kFull, en, o);
             const int ko = runs_pos<TV::NY>(rr, o, it);
-            bool ok = false;
-            float mx = 0.f, my = 0.f;
-            int ii = 0, jj = 0, kk = 0;
             const bool in = it < total;
             const int ko_c = in ? ko : (int)(eo >> 16);
             const float2 Pi = t.P[eo & 0xffffu], Pj = t.P[eo >> 16], Pk = t.P[ko_c];
-            if (in & pair_ok(Pi.x, Pi.y, Pk.x, Pk.y, B02) & pair_ok(Pj.x, Pj.y, Pk.x, Pk.y, B12)) {
-                ii = t.idx[eo & 0xffffu];
-                jj = t.idx[eo >> 16];
-                kk = t.idx[ko_c];
-                const float xs[3] = {__ldg(j.x + base0 + ii), __ldg(j.x + base1 + jj), __ldg(j.x + base2 + kk)};
-                const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
-                const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
-                ok = fit_pass(xs, ys, zs, c, mx, my);
-            }
-            const unsigned mask = __ballot_sync(kFull, ok);
-            if (mask) {
-                const int rk = __popc(mask & lanemask_lt()), np = __popc(mask);
-                int base = count;
-                if (sh_rank) {
-                    int b = 0;
-                    if (lane == 0) b = atomicAdd(sh_rank, np);
-                    base = __shfl_sync(kFull, b, 0);
-                }
-                if (EMIT && ok && base + rk < limit) {  // never past the unit's rows
-                    int32_t* r = rows + 3 * (int64_t)(base + rk);
-                    r[0] = ii;
-                    r[1] = jj;
-                    r[2] = kk;
-                }
-                if (ts.on) {
-                    int tb = ts.n;
-                    if (ts.sh_n) {
-                        int b = 0;
-                        if (lane == 0) b = atomicAdd(ts.sh_n, np);
-                        tb = __shfl_sync(kFull, b, 0);
-                    } else {
-                        ts.n += np;
+            const bool cand = in & pair_ok(Pi.x, Pi.y, Pk.x, Pk.y, B02) & pair_ok(Pj.x, Pj.y, Pk.x, Pk.y, B12);
+            if constexpr (!COMPACT) {
+                fit_and_record<EMIT>(j, t, lane, c, cand, (int)(eo & 0xffffu), (int)(eo >> 16), ko_c, ts, rows, limit,
+                                     unit, sh_rank, tag, count);
+            } else {
+                unsigned mask = __ballot_sync(kFull, cand);
+                while (mask) {  // warp-uniform: candidates of rank r go to lane pd.m + r
+                    const int np = __popc(mask), take = min(np, 32 - pd.m);
+                    const int r = lane - pd.m;
+                    const int src = nth_set_bit(mask, min(max(r, 0), np - 1));
+                    const uint32_t vp = __shfl_sync(kFull, eo, src);
+                    const int vk = __shfl_sync(kFull, ko_c, src);
+                    if (r >= 0 && r < take) {
+                        pd.pair = vp;
+                        pd.k = vk;
                     }
-                    if (ok && tb + rk < ts.cap) ts.T[tb + rk] = make_float2(mx, my);
-                }
-                if (!EMIT && j.tscr && !ts.norec) {  // record for the scatter pass
-                    unsigned long long b = 0;
-                    if (lane == 0) b = atomicAdd(&j.ctrl->scratch_n, (unsigned long long)np);
-                    b = __shfl_sync(kFull, b, 0) + rk;
-                    if (ok && b < (unsigned long long)j.tscr_cap) {
-                        TripEntry te;
-                        te.unit = (int32_t)unit;
-                        te.rank = base + rk;
-                        te.ijk = (unsigned long long)ii | ((unsigned long long)jj << 20) |
-                                 ((unsigned long long)kk << 40) | ((unsigned long long)tag << kTagShift);
-                        j.tscr[b] = te;
+                    pd.m += take;
+                    mask = take == np ? 0u : mask & ~((1u << nth_set_bit(mask, take)) - 1u);
+                    if (pd.m == 32) {
+                        fit_and_record<EMIT>(j, t, lane, c, true, (int)(pd.pair & 0xffffu), (int)(pd.pair >> 16),
+                                             pd.k, ts, rows, limit, unit, sh_rank, tag, count);
+                        pd.m = 0;
                     }
                 }
-                count += np;
             }
         }
     }
     __syncwarp();
+}
+
+// The pending triples of a block-path warp, at the end of its station.
+template <bool EMIT, class TV>
+__device__ __forceinline__ void flush_pending(const Job& j, const TV& t, int lane, const Cuts& c, TSink& ts,
+                                              int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag,
+                                              int& count, Pending& pd) {
+    if (pd.m > 0)
+        fit_and_record<EMIT>(j, t, lane, c, lane < pd.m, (int)(pd.pair & 0xffffu), (int)(pd.pair >> 16), pd.k, ts,
+                             rows, limit, unit, sh_rank, tag, count);
+    pd.m = 0;
 }
 
 template <class TV>
@@ -711,6 +782,7 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
     const int p0 = t.meta[0].pbase;
     const float B01 = __fadd_rn(t.meta[0].bmax, t.meta[1].bmax);
     int qn = 0, count = 0;
+    Pending pd;
     // rounds of 32 L0 hits: in order on the warp path; on the block path each
     // warp takes the next one from a block-shared counter
     auto next_round = [&]() {
@@ -753,7 +825,7 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
-                    drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
+                    drain<EMIT, SHARED>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count, pd);
                     qn = 0;
                 }
             }
@@ -774,7 +846,8 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
         }
     }
     __syncwarp();
-    drain<EMIT>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count);
+    drain<EMIT, SHARED>(j, t, queue, lane, c, qn, ts, rows, limit, unit, sh_rank, tag, count, pd);
+    if constexpr (SHARED) flush_pending<EMIT>(j, t, lane, c, ts, rows, limit, unit, sh_rank, tag, count, pd);
     return count;
 }
 
@@ -1168,13 +1241,31 @@ __device__ __forceinline__ void heavy_to_generic(const Job& j, int gi, int64_t e
 constexpr int kGiPlain = -1;  // the one-launch form: the same block goes on unpruned
 constexpr int kGiOwn = -2;    // a block that owns the whole event: to the unpruned list
 
+// Pulls the hit lines of station s of the event in sm.off into L2 (block
+// version of prefetch_hits_l2; addresses stay inside [o[0] & ~31, o[3])).
+template <class B>
+__device__ __forceinline__ void prefetch_station_block(const Job& j, const BlockSmem<B>& sm, int s) {
+    if (j.host_hits) return;
+    const int32_t h0 = sm.off[3 * s], h1 = sm.off[3 * s + 3];
+    for (int32_t a = (h0 & ~31) + 32 * (int)threadIdx.x; a < h1; a += 32 * B::THREADS) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.x + a));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.y + a));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(j.z + a));
+    }
+}
+
+// s_next: the station this block stages next (-1: none), whose lines start
+// towards L2 now; the station's own lines too, so that its second and third
+// layers arrive while the first is staged.
 template <bool EMIT, class B>
 __device__ bool heavy_unit(const Job& j, BlockSmem<B>& sm, const Cuts& c, int gi, int64_t e, int s, TSink& ts,
-                           const float2* T, uint8_t* alive, int nT, int& cnt) {
+                           const float2* T, uint8_t* alive, int nT, int& cnt, int s_next = -1) {
     using TV = TileView<B::NX, B::NY>;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t u = e * j.S + s;
     const int cnt_expected = EMIT ? j.unit_counts[u] : 0;
+    prefetch_station_block(j, sm, s);
+    if (s_next >= 0) prefetch_station_block(j, sm, s_next);
     const int st = stage_station_block(j, sm, s);
     if (st != 0) {
         if (tid == 0) {
@@ -1251,7 +1342,8 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
         const int s = station_of(si, j.trig);
         TSink ts{chain && si == 0, T, j.tlist_cap, &sm.s_nT, 0};
         int cnt = 0;
-        if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) return;
+        const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
+        if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) return;
         if (si > 0) {
             __syncthreads();
             continue;
@@ -1322,7 +1414,8 @@ __device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_
             if (j.unit_counts[e * S + s] == 0) continue;
             TSink ts{false, nullptr, 0, nullptr, 0};
             int cnt = 0;
-            heavy_unit<true>(j, sm, c, kGiOwn, e, s, ts, nullptr, nullptr, 0, cnt);
+            heavy_unit<true>(j, sm, c, kGiOwn, e, s, ts, nullptr, nullptr, 0, cnt,
+                             si + 1 < nproc ? station_of(si + 1, j.trig) : -1);
             __syncthreads();
         }
         return;
@@ -1334,7 +1427,8 @@ __device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_
         __syncthreads();
         TSink ts{chain && si == 0, ms.T, kTCap, &sm.s_nT, 0};
         int cnt = 0;
-        if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt)) return;
+        const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
+        if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt, sn)) return;
         __syncthreads();
         if (si > 0) continue;
         trig_count = cnt;
@@ -1732,7 +1826,8 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
             if (j.unit_counts[e * S + s] == 0) continue;
             TSink ts{false, nullptr, 0, nullptr, 0};
             int cnt = 0;
-            heavy_unit<true>(j, sm, c, kGiPlain, e, s, ts, nullptr, nullptr, 0, cnt);
+            heavy_unit<true>(j, sm, c, kGiPlain, e, s, ts, nullptr, nullptr, 0, cnt,
+                             si + 1 < nproc ? station_of(si + 1, j.trig) : -1);
             __syncthreads();
         }
         return false;
@@ -1756,7 +1851,8 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         __syncthreads();
         TSink ts{chain && si == 0, T, kPlainTCap, &sm.s_nT, 0};
         int cnt = 0;
-        if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt)) {
+        const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
+        if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) {
             __syncthreads();
             return j.ev_class[e] == kClsGeneric;
         }
