@@ -312,16 +312,21 @@ def run_serving(args, w, dev, jp, torch):
     it on that slot's stream while other slots copy or compute.  Latency =
     completion (outputs in host memory) - arrival.  Offered loads: the
     workload's 10^7 events/s, saturation (all requests at t=0), and 50/80/95 %
-    of the saturated throughput."""
+    of the saturated throughput; each load is `--requests` requests long.
+    Requests cycle over a pool of distinct timeslices and over a ring of
+    output buffers (a buffer is reused once its earlier request was waited
+    for); every served result is compared with the same timeslice run alone
+    (accept bits exactly, track counts and triplet total)."""
     import threading
 
     import synth
-    n_req = args.slices or 64
+    n_req = args.requests
     pool_n = min(args.pool, n_req)
-    sizes_all = synth.timeslice_sizes(w, n_req)
+    sizes_all = synth.timeslice_sizes(w, pool_n)
     p = jp.params(**params_kw(args, w))
     ctx = jp.Context(p, device=dev.index, hbm_budget=args.serve_budget_gb << 30)
     st = torch.cuda.current_stream(dev).cuda_stream
+    S = w.n_stations
     pool, e0 = [], 0
     t0 = time.perf_counter()
     for i in range(pool_n):
@@ -329,35 +334,40 @@ def run_serving(args, w, dev, jp, torch):
         b = synth.generate(w, e0, n)
         e0 += n
         h = {k: torch.from_numpy(b[k]).pin_memory() for k in ("x", "y", "z", "offsets")}
-        # exact triplet count of this timeslice, to size the slots
+        # the timeslice alone: exact triplet count (slot sizing) and the
+        # reference result of the isolation check
         d = {k: v.to(dev) for k, v in h.items()}
-        o = jp.jpsi_outputs()
-        ctx.check(jp.jpsi_run(ctx.ctx, jp.make_batch(d["x"], d["y"], d["z"], d["offsets"], n, b["n_hits"]), o, st))
-        pool.append({"h": h, "n": n, "hits": b["n_hits"], "trip": o.trip_needed})
-        del d
+        r = ctx.select(d["x"], d["y"], d["z"], d["offsets"], n)
+        ctx.check(r["status"])
+        pool.append({"h": h, "n": n, "hits": b["n_hits"], "trip": r["trip_needed"],
+                     "acc": r["accept_bits"].cpu().numpy().copy(), "tc_sum": int(r["track_counts"].sum().item())})
+        del d, r
     gen_s = time.perf_counter() - t0
     torch.cuda.empty_cache()
-    S = w.n_stations
     slot_events = max(q["n"] for q in pool)
     slot_hits = max(q["hits"] for q in pool)
     slot_trip = max(q["trip"] for q in pool)
     ctx.check(jp.jpsi_serve_start(ctx.ctx, args.slots, slot_events, slot_hits, slot_trip))
-    reqs = [pool[i % pool_n] for i in range(n_req)]
-    outs = []
-    for q in reqs:
-        n = q["n"]
-        ob = {"acc": torch.empty((n + 31) // 32, dtype=torch.int32, pin_memory=True),
-              "tc": torch.empty(n, dtype=torch.int32, pin_memory=True),
-              "toff": torch.empty(n * S + 1, dtype=torch.int64, pin_memory=True),
-              "trip": torch.empty((max(q["trip"], 1), 3), dtype=torch.int32, pin_memory=True)}
+    ring_n = 2 * args.slots + 2
+    ring = []
+    for _ in range(ring_n):
+        ob = {"acc": torch.empty((slot_events + 31) // 32, dtype=torch.int32, pin_memory=True),
+              "tc": torch.empty(slot_events, dtype=torch.int32, pin_memory=True),
+              "toff": torch.empty(slot_events * S + 1, dtype=torch.int64, pin_memory=True),
+              "trip": torch.empty((max(slot_trip, 1), 3), dtype=torch.int32, pin_memory=True)}
+        ring.append(ob)
+    batches = [jp.make_batch(q["h"]["x"], q["h"]["y"], q["h"]["z"], q["h"]["offsets"], q["n"], q["hits"])
+               for q in pool]
+    n_events = sum(pool[i % pool_n]["n"] for i in range(n_req))
+
+    def outputs(i):
+        q, ob = pool[i % pool_n], ring[i % ring_n]
         o = jp.jpsi_outputs()
         o.accept_bits, o.track_counts = ob["acc"].data_ptr(), ob["tc"].data_ptr()
         o.trip_off, o.triplets, o.trip_capacity = ob["toff"].data_ptr(), ob["trip"].data_ptr(), q["trip"]
-        hb = jp.make_batch(q["h"]["x"], q["h"]["y"], q["h"]["z"], q["h"]["offsets"], n, q["hits"])
-        outs.append((hb, o, ob))
-    n_events = sum(q["n"] for q in reqs)
+        return o
 
-    def run_load(rate):
+    def run_load(rate, check):
         mean = n_events / n_req
         if rate is None:
             arr = np.zeros(n_req)
@@ -366,19 +376,25 @@ def run_serving(args, w, dev, jp, torch):
             arr = np.cumsum(rng.exponential(mean / rate, size=n_req))
             arr -= arr[0]
         subs = [None] * n_req
+        outs = [None] * n_req
+        waited = [0]
+        cv = threading.Condition()
         t_start = time.perf_counter() + 0.05
 
         def submitter():
             for i in range(n_req):
+                with cv:  # the ring buffer of request i is free once request i - ring_n was waited for
+                    cv.wait_for(lambda: waited[0] > i - ring_n)
                 delay = t_start + arr[i] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
                 tc0 = time.perf_counter()
-                s_, tk = jp.jpsi_serve_submit(ctx.ctx, outs[i][0], outs[i][1])
+                outs[i] = outputs(i)
+                s_, tk = jp.jpsi_serve_submit(ctx.ctx, batches[i % pool_n], outs[i])
                 subs[i] = (s_, tk, tc0 - (t_start + arr[i]))
         th = threading.Thread(target=submitter)
         th.start()
-        lat, done = [], []
+        lat, done, mismatches = [], [], 0
         for i in range(n_req):
             while subs[i] is None:
                 time.sleep(0.0002)
@@ -388,35 +404,41 @@ def run_serving(args, w, dev, jp, torch):
             assert ws == 0 and rs == 0, (ws, rs)
             lat.append(queued + lat_lib)
             done.append(arr[i] + queued + lat_lib)
+            if check:
+                q, ob = pool[i % pool_n], ring[i % ring_n]
+                nw = (q["n"] + 31) // 32
+                same = (np.array_equal(ob["acc"].numpy()[:nw], q["acc"]) and
+                        int(ob["tc"][: q["n"]].sum().item()) == q["tc_sum"] and
+                        outs[i].trip_needed == q["trip"])
+                mismatches += 0 if same else 1
+            with cv:
+                waited[0] = i + 1
+                cv.notify_all()
         th.join()
         span = max(done)
-        return {"offered_events_per_s": None if rate is None else rate, "sustained_events_per_s": n_events / span,
-                "latency_ms": {k: 1000 * v for k, v in percentiles(lat).items()}}
+        out = {"offered_events_per_s": None if rate is None else rate, "sustained_events_per_s": n_events / span,
+               "requests": n_req, "latency_ms": {k: 1000 * v for k, v in percentiles(lat).items()}}
+        if check:
+            out["results_equal_solo"] = mismatches == 0
+        return out
 
-    run_load(None)  # warm-up: graphs, buffers
-    sat = run_load(None)
+    run_load(None, False)  # warm-up: graphs, buffers
+    sat = run_load(None, True)
     cap = sat["sustained_events_per_s"]
-    loads = [run_load(w.extra["rate_events_per_s"])]
+    loads = [run_load(w.extra["rate_events_per_s"], True)]
     for f in (0.5, 0.8, 0.95):
-        r = run_load(f * cap)
+        r = run_load(f * cap, True)
         r["fraction_of_saturation"] = f
         loads.append(r)
-    # isolation: a served result equals the same timeslice run alone
-    hb, o, ob = outs[0]
-    solo = {"acc": torch.empty_like(ob["acc"]), "tc": torch.empty_like(ob["tc"]), "toff": torch.empty_like(ob["toff"]),
-            "trip": torch.empty_like(ob["trip"])}
-    o2 = jp.jpsi_outputs()
-    o2.accept_bits, o2.track_counts = solo["acc"].data_ptr(), solo["tc"].data_ptr()
-    o2.trip_off, o2.triplets, o2.trip_capacity = solo["toff"].data_ptr(), solo["trip"].data_ptr(), o.trip_capacity
     ctx.check(jp.jpsi_serve_stop(ctx.ctx))
-    ctx.check(jp.jpsi_run_host(ctx.ctx, hb, o2, st))
-    same = all(torch.equal(solo[k], ob[k]) for k in ("acc", "tc", "toff"))
     line = {"metric": METRIC, "value": cap, "unit": UNIT, "n_gpus": 1, "steps": len(loads) + 2, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "requests": n_req, "distinct_timeslices": pool_n, "events": n_events,
-                       "slots": args.slots, "slot_events": slot_events, "slot_hits": slot_hits,
-                       "hbm_budget_gb": args.serve_budget_gb, "mode": args.mode},
-            "saturation": sat, "loads": loads, "isolation_counts_equal": bool(same), "generate_s": gen_s}
+            "config": {"workload": w.name, "requests_per_load": n_req, "distinct_timeslices": pool_n,
+                       "events_per_load": n_events, "slots": args.slots, "slot_events": slot_events,
+                       "slot_hits": slot_hits, "hbm_budget_gb": args.serve_budget_gb, "mode": args.mode},
+            "saturation": sat, "loads": loads,
+            "isolation": all(r.get("results_equal_solo", True) for r in [sat] + loads),
+            "generate_s": gen_s}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
     print(json.dumps(line), flush=True)
@@ -501,6 +523,7 @@ def main():
     ap.add_argument("--stress-budget-gb", type=int, default=160)
     ap.add_argument("--pool", type=int, default=8, help="distinct timeslices generated for the stream workload")
     ap.add_argument("--slots", type=int, default=5)
+    ap.add_argument("--requests", type=int, default=1000, help="requests per offered load (stream workload)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     args = ap.parse_args()
     rank, world, local = dist_info()
