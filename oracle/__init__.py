@@ -32,11 +32,14 @@ class Params(ctypes.Structure):
         ("min_candidates", ctypes.c_int32),
         ("t_xz", ctypes.c_float),
         ("t_yz", ctypes.c_float),
+        ("distinct_hits", ctypes.c_int32),
     ]
 
 
-def params(n_stations=4, mode=MODE_CHAIN, t_xz=0.25, t_yz=None, ndf=2, min_candidates=2, trigger_station=None):
+def params(n_stations=4, mode=MODE_CHAIN, t_xz=0.25, t_yz=None, ndf=2, min_candidates=2, trigger_station=None,
+           distinct_hits=0):
     p = Params()
+    p.distinct_hits = distinct_hits
     p.n_stations = n_stations
     p.trigger_station = n_stations - 1 if trigger_station is None else trigger_station
     p.mode = mode

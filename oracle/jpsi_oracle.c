@@ -28,7 +28,12 @@
  *     is a track candidate iff each other station holds a passing triplet t
  *     whose three hits, taken against T's slopes (no refit), have a summed
  *     squared residual <= the same thresholds in both planes.  PAPER mode: the
- *     candidates are the passing trigger triplets (step 3 as printed).
+ *     candidates are the passing trigger triplets (step 3 as printed);
+ *   - "at least two triplets" (step 3) counts any candidates by default; with
+ *     distinct_hits = 1 it needs min_candidates candidates (at most 2) no two
+ *     of which share a hit: two candidates share a hit when they use the same
+ *     hit of the same trigger-station layer (one hit, one particle).  Track
+ *     counts stay the number of candidates.
  *
  * The pair early-out (brute = 0) skips (i, j) when
  *     |u_i/z_i - u_j/z_j| > (sqrt(C)(1+1e-5) + 1e-3) (1/z_i + 1/z_j)
@@ -132,6 +137,7 @@ typedef struct {
     int32_t i, j, k;   /* layer-local hit indices */
     int32_t hi, hj, hk;/* batch hit indices */
     double mx, my;     /* fitted slopes (the FP32 values, exactly, in FP32 mode) */
+    int cand;          /* a candidate (trigger station only) */
 } trip_t;
 
 typedef struct {
@@ -182,6 +188,7 @@ typedef struct {
     int brute, fp64, want_trip;
     int32_t *unit_counts;   /* [n_events*S] */
     int32_t *track_counts;  /* [n_events] */
+    uint8_t *disjoint;      /* [n_events]: two candidates share no hit (distinct_hits) */
     /* per thread */
     int64_t e_begin, e_end;
     tripvec per_station[JO_MAX_STATIONS];
@@ -285,14 +292,13 @@ static int process_event(worker_t *w, int64_t e) {
         const int rc = process_station(w, e, s, &w->per_station[s]);
         if (rc != JO_OK) return rc;
     }
-    /* step 3 (PAPER) or chaining (CHAIN) */
+    /* step 3 (PAPER) or chaining (CHAIN): a candidate is a passing trigger
+     * triplet (PAPER) or one compatible with every other station (CHAIN) */
     const tripvec *T = &w->per_station[trig];
     int64_t n_cand = 0;
-    if (p->mode == JO_MODE_PAPER) {
-        n_cand = T->n;
-    } else {
-        for (int64_t a = 0; a < T->n; ++a) {
-            int ok = 1;
+    for (int64_t a = 0; a < T->n; ++a) {
+        int ok = 1;
+        if (p->mode == JO_MODE_CHAIN) {
             for (int s = 0; s < S && ok; ++s) {
                 if (s == trig) continue;
                 const tripvec *ts = &w->per_station[s];
@@ -300,10 +306,21 @@ static int process_event(worker_t *w, int64_t e) {
                 for (int64_t b = 0; b < ts->n && !found; ++b) found = compatible(w, &T->v[a], &ts->v[b]);
                 ok = found;
             }
-            n_cand += ok;
         }
+        T->v[a].cand = ok;
+        n_cand += ok;
     }
     w->track_counts[e] = n_cand > INT32_MAX ? INT32_MAX : (int32_t)n_cand;
+    if (w->disjoint) {
+        /* two candidates with no hit in common (same layer, same index) */
+        int found = 0;
+        for (int64_t a = 0; a < T->n && !found; ++a) {
+            if (!T->v[a].cand) continue;
+            for (int64_t b = a + 1; b < T->n && !found; ++b)
+                found = T->v[b].cand && T->v[a].i != T->v[b].i && T->v[a].j != T->v[b].j && T->v[a].k != T->v[b].k;
+        }
+        w->disjoint[e] = (uint8_t)found;
+    }
     for (int s = 0; s < S; ++s) {
         const tripvec *ts = &w->per_station[s];
         if (ts->n > INT32_MAX) return JO_EINVAL;
@@ -334,6 +351,7 @@ static int params_ok(const jo_params *p) {
     if (p->trigger_station < 0 || p->trigger_station >= p->n_stations) return 0;
     if (p->mode != JO_MODE_PAPER && p->mode != JO_MODE_CHAIN) return 0;
     if (p->ndf < 1 || p->min_candidates < 0) return 0;
+    if (p->distinct_hits != 0 && (p->distinct_hits != 1 || p->min_candidates > 2)) return 0;
     if (!(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) || isinf(p->t_xz) || isinf(p->t_yz)) return 0;
     return 1;
 }
@@ -362,9 +380,11 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
     const int64_t n_units = n_events * S;
     int32_t *uc = unit_counts ? unit_counts : (int32_t *)malloc((size_t)n_units * sizeof(int32_t));
     int32_t *tc = track_counts ? track_counts : (int32_t *)malloc((size_t)n_events * sizeof(int32_t));
-    if (!uc || !tc) {
+    uint8_t *dj = p->distinct_hits ? (uint8_t *)calloc((size_t)n_events, 1) : NULL;
+    if (!uc || !tc || (p->distinct_hits && !dj)) {
         if (!unit_counts) free(uc);
         if (!track_counts) free(tc);
+        free(dj);
         return JO_ENOMEM;
     }
     if (n_threads < 1) n_threads = 1;
@@ -387,7 +407,7 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
             w->ky = sqrt(fmax((double)cy, w->cy64)) * (1.0 + 1e-5) + 1e-3;
             w->brute = brute; w->fp64 = fp64;
             w->want_trip = triplets != NULL;
-            w->unit_counts = uc; w->track_counts = tc;
+            w->unit_counts = uc; w->track_counts = tc; w->disjoint = dj;
             w->e_begin = n_events * t / n_threads;
             w->e_end = n_events * (t + 1) / n_threads;
         }
@@ -412,7 +432,8 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
         if (accept_bits) {
             memset(accept_bits, 0, (size_t)((n_events + 31) / 32) * sizeof(uint32_t));
             for (int64_t e = 0; e < n_events; ++e)
-                if (tc[e] >= p->min_candidates) accept_bits[e >> 5] |= 1u << (e & 31);
+                if (p->distinct_hits && p->min_candidates == 2 ? dj[e] : tc[e] >= p->min_candidates)
+                    accept_bits[e >> 5] |= 1u << (e & 31);
         }
         if (triplets) {
             if (total > trip_capacity) {
@@ -436,6 +457,7 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
         }
     free(ws);
     free(th);
+    free(dj);
     if (!unit_counts) free(uc);
     if (!track_counts) free(tc);
     return rc;

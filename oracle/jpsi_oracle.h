@@ -24,6 +24,9 @@ typedef struct {
     int32_t ndf;             /* degrees of freedom of the fit (2: three hits, one slope) */
     int32_t min_candidates;  /* accept if #candidates >= this (2, Sec. 3.2 step 3) */
     float t_xz, t_yz;        /* MSD-per-dof thresholds (Sec. 3.2 step 2b), cm^2 */
+    int32_t distinct_hits;   /* 0: step 3 counts any candidates; 1: the event needs
+                                min_candidates (<= 2) candidates no two of which share
+                                a hit of the trigger station */
 } jo_params;
 
 /*

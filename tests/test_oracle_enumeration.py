@@ -42,6 +42,21 @@ def _tiny_events(rng, n_events, S, max_hits=4):
     return events
 
 
+def _shared_hit_event(S, third):
+    """Every station: two close tracks in layers 0 and 2 and one middle-layer
+    hit between them, so the trigger station's candidates all use that hit;
+    `third` adds a separate track."""
+    ev = []
+    for s in range(S):
+        for l in range(3):
+            z = 120.0 + 35.0 * s + 10.0 * (l - 1)
+            hits = [(0.1 * z + 0.4, 0.1 * z, z)] if l == 1 else [(0.1 * z, 0.1 * z, z), (0.1 * z + 0.8, 0.1 * z, z)]
+            if third:
+                hits.append((-0.2 * z, 0.15 * z, z))
+            ev.append(hits)
+    return ev
+
+
 class Restated:
     """Sec. 3.2 steps 1-3 (plus the CHAIN rule) over Python lists."""
 
@@ -74,43 +89,47 @@ class Restated:
         return self._compat[key]
 
     def event(self, ev):
+        """Passing triplets per station, the candidates' (i, j, k), and whether
+        two candidates share no hit."""
         stations = [ev[3 * s: 3 * s + 3] for s in range(self.S)]
         per = [self.passing(st) if (self.mode == 1 or s == self.trig) else [] for s, st in enumerate(stations)]
         T = per[self.trig]
         if self.mode == 0 or self.S == 1:
-            n_cand = len(T)
+            cands = [ijk for ijk, _ in T]
         else:
-            n_cand = 0
-            for _, Th in T:
-                if all(any(self.compatible(Th, th) for _, th in per[s]) for s in range(self.S) if s != self.trig):
-                    n_cand += 1
-        return per, n_cand
+            cands = [ijk for ijk, Th in T
+                     if all(any(self.compatible(Th, th) for _, th in per[s]) for s in range(self.S) if s != self.trig)]
+        disjoint = any(all(a != b for a, b in zip(c1, c2)) for c1, c2 in itertools.combinations(cands, 2))
+        return per, len(cands), disjoint
 
 
 @pytest.mark.parametrize("S,mode,trig", [(2, 1, 1), (3, 1, 2), (4, 1, 1), (3, 0, 2), (1, 1, 0)])
-@pytest.mark.parametrize("ndf,minc", [(2, 2), (3, 1), (2, 3)])
-def test_enumeration_restated(oracle_mod, S, mode, trig, ndf, minc):
+@pytest.mark.parametrize("ndf,minc,distinct", [(2, 2, 0), (3, 1, 0), (2, 3, 0), (2, 2, 1), (3, 1, 1)])
+def test_enumeration_restated(oracle_mod, S, mode, trig, ndf, minc, distinct):
     rng = np.random.default_rng(1000 * S + 10 * mode + trig + 7 * ndf + minc)
     t = 0.3
-    events = _tiny_events(rng, 40, S)
+    events = _tiny_events(rng, 40, S) + [_shared_hit_event(S, False), _shared_hit_event(S, True)]
     b = make_batch(events, S)
     R = Restated(oracle_mod, S, mode, t, ndf, minc, trig)
-    counts, tcounts, rows = [], [], []
+    counts, tcounts, rows, accepts = [], [], [], []
     for e, ev in enumerate(events):
-        per, n_cand = R.event(ev)
+        per, n_cand, disjoint = R.event(ev)
         tcounts.append(n_cand)
+        accepts.append(disjoint if (distinct and minc == 2) else n_cand >= minc)
         for s in range(S):
             counts.append(len(per[s]))
             rows += [(e * S + s,) + ijk for ijk, _ in per[s]]
     # the events exercise chaining and both sides of the accept rule
     assert min(tcounts) < minc <= max(tcounts), (min(tcounts), max(tcounts))
+    if distinct and minc == 2:  # some event needs the rule: two candidates, every pair sharing a hit
+        assert any(c >= 2 and not a for c, a in zip(tcounts, accepts)), tcounts
     for brute in (False, True):
-        r = oracle_mod.run(oracle_mod.params(S, mode, t_xz=t, ndf=ndf, min_candidates=minc, trigger_station=trig),
-                           b, brute=brute)
+        r = oracle_mod.run(oracle_mod.params(S, mode, t_xz=t, ndf=ndf, min_candidates=minc, trigger_station=trig,
+                                             distinct_hits=distinct), b, brute=brute)
         assert r["status"] == 0
         assert list(r["unit_counts"]) == counts
         assert list(r["track_counts"]) == tcounts
         assert list(r["trip_off"]) == [0] + list(np.cumsum(counts))
-        assert list(accept_list(r["accept_bits"], len(events))) == [c >= minc for c in tcounts]
+        assert list(accept_list(r["accept_bits"], len(events))) == accepts
         got = sorted_triplets(r["trip_off"], r["triplets"], len(events) * S)
         assert [tuple(v) for v in got] == sorted(rows)

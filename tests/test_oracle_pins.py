@@ -385,3 +385,36 @@ def test_min_candidates_threshold(oracle_mod):
         r = oracle_mod.run(oracle_mod.params(1, 0, t_xz=0.01, min_candidates=minc), b)
         assert r["status"] == 0 and list(r["track_counts"]) == [2, 0]
         assert list(accept_list(r["accept_bits"], 2)) == acc, minc
+
+
+def _shared_hit_event(with_third_track):
+    """One station, t = 10 cm^2: two nearby tracks whose layer-0 and layer-2
+    hits combine with the single layer-1 hit in all four ways, so every
+    candidate uses that hit; optionally a third track far away."""
+    z = [120.0, 130.0, 140.0]
+    l0 = [(0.1 * z[0], 0.1 * z[0], z[0]), (0.1 * z[0] + 3.0, 0.1 * z[0], z[0])]
+    l1 = [(0.1 * z[1] + 1.5, 0.1 * z[1], z[1])]
+    l2 = [(0.1 * z[2], 0.1 * z[2], z[2]), (0.1 * z[2] + 3.0, 0.1 * z[2], z[2])]
+    if with_third_track:
+        for layer, zz in zip((l0, l1, l2), z):
+            layer.append((-0.2 * zz, 0.15 * zz, zz))
+    return [l0, l1, l2]
+
+
+def test_distinct_hits_candidates_sharing_a_hit_count_as_one(oracle_mod):
+    # Sec. 3.2 step 3, "at least two triplets", read with distinct_hits = 1:
+    # two candidates that use the same hit are one track, not two
+    b = make_batch([_shared_hit_event(False), _shared_hit_event(True)], 1)
+    plain = oracle_mod.run(oracle_mod.params(1, 0, t_xz=10.0), b)
+    dist = oracle_mod.run(oracle_mod.params(1, 0, t_xz=10.0, distinct_hits=1), b)
+    assert plain["status"] == 0 and dist["status"] == 0
+    assert list(plain["track_counts"]) == [4, 5] and list(dist["track_counts"]) == [4, 5]
+    assert list(accept_list(plain["accept_bits"], 2)) == [True, True]
+    assert list(accept_list(dist["accept_bits"], 2)) == [False, True]
+    # min_candidates 0 and 1 read the same with and without the rule
+    for minc, acc in ((0, [True, True]), (1, [True, True])):
+        r = oracle_mod.run(oracle_mod.params(1, 0, t_xz=10.0, min_candidates=minc, distinct_hits=1), b)
+        assert list(accept_list(r["accept_bits"], 2)) == acc
+    # more than two pairwise disjoint candidates is not defined: refused
+    r = oracle_mod.run(oracle_mod.params(1, 0, t_xz=10.0, min_candidates=3, distinct_hits=1), b)
+    assert r["status"] == oracle_mod.EINVAL
