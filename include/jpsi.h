@@ -91,14 +91,19 @@ typedef enum { JPSI_MODE_PAPER = 0, JPSI_MODE_CHAIN = 1 } jpsi_mode;
 
 /* Selection parameters (Sec. 3.2).  Defaults of the paper: ndf = 2 (three
  * hits, one slope), min_candidates = 2, trigger_station = n_stations - 1,
- * t_xz = 0.03 and t_yz = 0.025 cm^2 (step 2b). */
+ * t_xz = 0.03 and t_yz = 0.025 cm^2 (step 2b).
+ * distinct_hits = 1 reads step 3's "at least two triplets" as candidates
+ * that share no hit: the event is accepted only if it holds min_candidates
+ * (at most 2) candidates no two of which use the same hit of a
+ * trigger-station layer.  track_counts stay the number of candidates. */
 typedef struct {
     int32_t n_stations;      /* 1 .. 16 */
     int32_t trigger_station; /* 0 .. n_stations-1 */
     int32_t mode;            /* jpsi_mode */
     int32_t ndf;             /* >= 1 */
-    int32_t min_candidates;  /* >= 0 */
+    int32_t min_candidates;  /* >= 0 (<= 2 with distinct_hits) */
     float t_xz, t_yz;        /* >= 0, finite */
+    int32_t distinct_hits;   /* 0 (default) or 1 */
 } jpsi_params;
 
 typedef struct {
@@ -267,6 +272,8 @@ jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);
  * Only events that fit the warp tiles (192 hits per layer, 384 per station, at
  * most 64 passing trigger triplets in CHAIN mode, finite pruning bounds) are
  * handled; a batch holding any other event returns JPSI_EINVAL (use jpsi_run).
+ * distinct_hits = 1 is not supported here (JPSI_EINVAL): it changes accept
+ * bits only, which this entry point does not return.
  * The call is synchronous on `cuda_stream`.  The first call on a device looks
  * up the array's device address for that device (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array and

@@ -34,7 +34,7 @@ class JpsiError(RuntimeError):
 class jpsi_params(ctypes.Structure):
     _fields_ = [("n_stations", ctypes.c_int32), ("trigger_station", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("ndf", ctypes.c_int32), ("min_candidates", ctypes.c_int32), ("t_xz", ctypes.c_float),
-                ("t_yz", ctypes.c_float)]
+                ("t_yz", ctypes.c_float), ("distinct_hits", ctypes.c_int32)]
 
 
 class jpsi_batch(ctypes.Structure):
@@ -213,8 +213,9 @@ def jpsi_select_noalloc(params: jpsi_params, batch: jpsi_batch, track_counts, un
 # --------------------------------------------------------------- helpers
 
 def params(n_stations=4, mode=JPSI_MODE_CHAIN, t_xz=0.25, t_yz=None, ndf=2, min_candidates=2,
-           trigger_station=None) -> jpsi_params:
+           trigger_station=None, distinct_hits=0) -> jpsi_params:
     p = jpsi_params()
+    p.distinct_hits = distinct_hits
     p.n_stations = n_stations
     p.trigger_station = n_stations - 1 if trigger_station is None else trigger_station
     p.mode = mode

@@ -61,6 +61,7 @@ struct RunState {
     Ctrl* h_ctrl = nullptr;   // pinned
     DevBuf unit_counts, track_counts, ev_class, mlist, hlist, glist, block_sums, trip_off, tscr, tlist, talive;
     DevBuf tpool, tpool_alive, hT;
+    DevBuf dpair, tlist_ijk, tpool_ijk;  // distinct_hits
     DevBuf zfill, ztab;  // per-hit z filled from a batch's z_layer table; the table on the device
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
     Graph g_light, g_rest, g_emit, g_scatter;
@@ -181,6 +182,7 @@ jpsi_status params_ok(const jpsi_params* p) {
     if (p->trigger_station < 0 || p->trigger_station >= p->n_stations) return JPSI_EINVAL;
     if (p->mode != JPSI_MODE_PAPER && p->mode != JPSI_MODE_CHAIN) return JPSI_EINVAL;
     if (p->ndf < 1 || p->min_candidates < 0) return JPSI_EINVAL;
+    if (p->distinct_hits != 0 && (p->distinct_hits != 1 || p->min_candidates > 2)) return JPSI_EINVAL;
     if (!(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) || std::isinf(p->t_xz) || std::isinf(p->t_yz)) return JPSI_EINVAL;
     return JPSI_OK;
 }
@@ -242,6 +244,11 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     if ((st = ensure(c, rs.tpool, (size_t)tp * sizeof(float2), "trigger pool")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.tpool_alive, (size_t)tp, "trigger pool")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.hT, (size_t)std::max<int64_t>(ne, 1) * sizeof(int2), "event list")) != JPSI_OK) return st;
+    if (c->p.distinct_hits &&
+        ((st = ensure(c, rs.dpair, (size_t)std::max<int64_t>(ne, 1), "disjoint flags")) != JPSI_OK ||
+         (st = ensure(c, rs.tlist_ijk, tl * sizeof(unsigned long long), "trigger lists")) != JPSI_OK ||
+         (st = ensure(c, rs.tpool_ijk, (size_t)tp * sizeof(unsigned long long), "trigger pool")) != JPSI_OK))
+        return st;
     const int64_t ntiles = (nu + 4095) / 4096 + 1;
     if ((st = ensure(c, rs.block_sums, (size_t)ntiles * 8, "scan")) != JPSI_OK) return st;
     if (!o->track_counts && (st = ensure(c, rs.track_counts, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts")))
@@ -261,6 +268,10 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.trig = c->p.trigger_station;
     j.mode = c->p.mode;
     j.minc = c->p.min_candidates;
+    j.distinct = c->p.distinct_hits;
+    j.dpair = (uint8_t*)rs.dpair.p;
+    j.tlist_ijk = (unsigned long long*)rs.tlist_ijk.p;
+    j.tpool_ijk = (unsigned long long*)rs.tpool_ijk.p;
     j.cx = c->cx;
     j.cy = c->cy;
     j.K = c->K;
@@ -280,6 +291,8 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.tpool = (float2*)rs.tpool.p;
     j.tpool_alive = (uint8_t*)rs.tpool_alive.p;
     j.tpool_cap = (int64_t)std::min(rs.tpool.bytes / sizeof(float2), rs.tpool_alive.bytes);
+    if (c->p.distinct_hits)
+        j.tpool_cap = std::min<int64_t>(j.tpool_cap, (int64_t)(rs.tpool_ijk.bytes / sizeof(unsigned long long)));
     j.hT = (int2*)rs.hT.p;
     j.accept_bits = o->accept_bits;
     j.trip_off = o->trip_off ? o->trip_off : (int64_t*)rs.trip_off.p;
@@ -352,6 +365,9 @@ void state_free(jpsi_ctx* c, RunState& rs) {
     release(c, rs.tpool);
     release(c, rs.tpool_alive);
     release(c, rs.hT);
+    release(c, rs.dpair);
+    release(c, rs.tlist_ijk);
+    release(c, rs.tpool_ijk);
     release(c, rs.zfill);
     release(c, rs.ztab);
     release(c, rs.block_sums);
@@ -445,6 +461,8 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     const int64_t ne = b->n_events;
     cudaError_t e;
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
+    if (c->p.distinct_hits && ne > 0 && (e = cudaMemsetAsync(rs.dpair.p, 0, (size_t)ne, st)) != cudaSuccess)
+        return cuda_fail(c, e, "flag reset");
     const bool timing = c->timing.load();
     if (batched && (s = capture_graphs(c, rs)) != JPSI_OK) return s;
     if (timing) cudaEventRecord(rs.ev[0], st);
@@ -460,6 +478,7 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "count phase");
     const Ctrl ctl = *rs.h_ctrl;
     if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
+    if (ctl.status & kStNoPool) return fail(c, JPSI_ENOMEM, "distinct_hits: candidates exceed the trigger pool");
     o->trip_needed = ctl.trip_total;
     if (!o->triplets) {
         add_timing(c, rs, launches, false);
@@ -704,6 +723,8 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "chunk upload");
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
+    if (c->p.distinct_hits && (e = cudaMemsetAsync(rs.dpair.p, 0, (size_t)ne, st)) != cudaSuccess)
+        return cuda_fail(c, e, "flag reset");
     k = 0;
     for (int64_t e0 = 0; e0 < ne; e0 += cs, ++k) {
         const int64_t e1 = std::min(ne, e0 + cs);
@@ -724,6 +745,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         return cuda_fail(c, e, "count phase");
     const Ctrl ctl = *rs.h_ctrl;
     if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
+    if (ctl.status & kStNoPool) return fail(c, JPSI_ENOMEM, "distinct_hits: candidates exceed the trigger pool");
     ho->trip_needed = ctl.trip_total;
     s = JPSI_OK;
     if (ho->triplets && ctl.trip_total > ho->trip_capacity) {

@@ -14,7 +14,18 @@ enum : int32_t {
     kStInvalid = 1,        // malformed offsets or z <= 0
     kStEmitMismatch = 2,   // emit pass found a different count than the count pass (internal error)
     kStNoScratch = 4,      // a triplet index did not fit the scratch entry format
+    kStNoPool = 8,         // distinct_hits: the candidates' hits found no room in the trigger pool
 };
+
+// Layer-local indices (i, j, k) of a trigger triplet, 21 bits each.
+__host__ __device__ inline unsigned long long pack_ijk(int i, int j, int k) {
+    return (unsigned long long)i | ((unsigned long long)j << 21) | ((unsigned long long)k << 42);
+}
+// Do two packed triplets use no common hit (each layer's index differs)?
+__host__ __device__ inline bool ijk_disjoint(unsigned long long a, unsigned long long b) {
+    const unsigned long long d = a ^ b, m = (1ull << 21) - 1;
+    return (d & m) && ((d >> 21) & m) && ((d >> 42) & m);
+}
 
 // A passing triplet recorded by the counting pass: unit, rank inside the
 // unit, (i, j, k) packed 20 bits each, and in bits 60-62 the class of the
@@ -64,6 +75,7 @@ struct Job {
     int64_t n_hits;
     int64_t ev_begin, ev_count;   // events the warp kernels take from the batch (all by default)
     int32_t S, trig, mode, minc;
+    int32_t distinct;             // distinct_hits: accept bits from dpair when minc == 2
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
     int32_t cap_small, cap_medium;// most hits per layer on the small / medium warp tile (<= the tile's own)
@@ -83,6 +95,9 @@ struct Job {
     uint8_t* tpool_alive;         // [tpool_cap]
     int64_t tpool_cap;
     int2* hT;                     // [n_events] per block-tile list entry: pool start, slope count or state
+    uint8_t* dpair;               // [n_events] distinct_hits: two candidates share no hit
+    unsigned long long* tlist_ijk;// [heavy blocks * tlist_cap] distinct_hits: candidates' packed hits
+    unsigned long long* tpool_ijk;// [tpool_cap] distinct_hits
     uint32_t* accept_bits;        // may be null
     int64_t* trip_off;            // [n_units + 1]
     int64_t* block_sums;          // scan scratch

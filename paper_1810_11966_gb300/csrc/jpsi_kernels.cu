@@ -118,6 +118,7 @@ struct WarpTile {
     uint16_t idx[Cfg::HCAP];
     uint32_t queue[kQCap];      // pair queue (enumeration)
     float2 T[kTCap];            // trigger triplet slopes
+    unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
     uint8_t alive[kTCap];
     alignas(4) uint16_t bst[3 * Cfg::NC + 1];  // cell starts (cell counts while a layer is staged)
     LayerMeta meta[3];
@@ -144,6 +145,53 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// distinct_hits: do the candidates ijk[0, n) (those with alive set, when
+// alive is given) hold two that use no common hit?  The warp walks the pair
+// matrix in 32 x 32 tiles (candidate b of a tile comes by shuffle) and stops
+// at the first tile with such a pair; warp-uniform result.  Block version:
+// the warps take the rows of tiles in turn and stop at a block-shared flag.
+__device__ __forceinline__ bool pair_tile_rows(const unsigned long long* ijk, const uint8_t* alive, int n, int a0,
+                                               int lane) {
+    const int a = a0 + lane;
+    const bool va = a < n && (!alive || alive[a]);
+    const unsigned long long ca = va ? ijk[a] : 0ull;
+    for (int b0 = a0; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        const bool vb = b < n && (!alive || alive[b]);
+        const unsigned long long cb = vb ? ijk[b] : 0ull;
+        bool f = false;
+        for (int q = 0; q < 32; ++q) {
+            const unsigned long long cq = __shfl_sync(0xffffffffu, cb, q);
+            const bool vq = __shfl_sync(0xffffffffu, vb, q);
+            f |= va & vq & (b0 + q > a) && ijk_disjoint(ca, cq);
+        }
+        if (__any_sync(0xffffffffu, f)) return true;
+    }
+    return false;
+}
+
+__device__ bool warp_disjoint_pair(const unsigned long long* ijk, const uint8_t* alive, int n, int lane) {
+    for (int a0 = 0; a0 < n; a0 += 32)
+        if (pair_tile_rows(ijk, alive, n, a0, lane)) return true;
+    return false;
+}
+
+// All threads of the block call it; sh_flag is block-shared scratch.
+template <int THREADS>
+__device__ bool block_disjoint_pair(const unsigned long long* ijk, const uint8_t* alive, int n, int* sh_flag) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) *sh_flag = 0;
+    __syncthreads();
+    for (int a0 = 32 * wp; a0 < n; a0 += THREADS) {
+        if (__any_sync(0xffffffffu, *(volatile int*)sh_flag)) break;  // warp-uniform
+        if (pair_tile_rows(ijk, alive, n, a0, lane)) {
+            if (lane == 0) *(volatile int*)sh_flag = 1;
+            break;
+        }
+    }
+    return __syncthreads_or(*(volatile int*)sh_flag);
 }
 
 // Min/max of non-NaN floats through the integer reduction unit: the map is
@@ -562,6 +610,7 @@ struct TSink {
     int* sh_n;  // block-shared counter, or null
     int n;      // warp-local counter when sh_n is null
     bool norec = false;  // a repeated enumeration: record no triplet entries
+    unsigned long long* ijk = nullptr;  // distinct_hits: the triplets' packed hits beside T
 };
 
 // Items of up to 32 lanes laid end to end: lane i owns items [excl, excl +
@@ -661,7 +710,10 @@ __device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int la
             } else {
                 ts.n += np;
             }
-            if (ok && tb + rk < ts.cap) ts.T[tb + rk] = make_float2(mx, my);
+            if (ok && tb + rk < ts.cap) {
+                ts.T[tb + rk] = make_float2(mx, my);
+                if (ts.ijk) ts.ijk[tb + rk] = pack_ijk(ii, jj, kk);
+            }
         }
         if (!EMIT && j.tscr && !ts.norec) {  // record for the scatter pass
             unsigned long long b = 0;
@@ -1074,6 +1126,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
     }
     const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
+    ts.ijk = j.distinct ? w.Tijk : nullptr;
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
@@ -1093,7 +1146,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
             if (lane == 0) push_event(j, e, kClsGeneric);
             return;
         }
-        ts.on = chain && s == j.trig;
+        ts.on = (chain || j.distinct) && s == j.trig;  // the trigger triplets: CHAIN slopes, candidates' hits
         const int cnt = enum_station<false, false>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
                                             nullptr);
         if (ts.on) {
@@ -1124,6 +1177,10 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         int a = 0;
         for (int ti = lane; ti < ts.n; ti += 32) a += w.alive[ti];
         tc = __reduce_add_sync(kFull, a);
+    }
+    if (j.distinct) {  // ts.n is warp-uniform
+        const bool f = ts.n >= 2 && warp_disjoint_pair(w.Tijk, chain ? w.alive : nullptr, ts.n, lane);
+        if (lane == 0) j.dpair[e] = f;
     }
     if (lane == 0) {
         j.track_counts[e] = tc;
@@ -1337,10 +1394,12 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
     }
     float2* T = j.tlist + (int64_t)blockIdx.x * j.tlist_cap;
     uint8_t* alive = j.talive + (int64_t)blockIdx.x * j.tlist_cap;
+    unsigned long long* ijk = j.distinct ? j.tlist_ijk + (int64_t)blockIdx.x * j.tlist_cap : nullptr;
     int trig_count = 0, nT = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
-        TSink ts{chain && si == 0, T, j.tlist_cap, &sm.s_nT, 0};
+        TSink ts{(chain || j.distinct) && si == 0, T, j.tlist_cap, &sm.s_nT, 0};
+        ts.ijk = ijk;
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
         if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) return;
@@ -1349,11 +1408,17 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
             continue;
         }
         trig_count = cnt;
-        if (!chain) break;
         nT = sm.s_nT;
         if (nT > j.tlist_cap) {
             if (tid == 0) heavy_to_generic(j, gi, e);
             return;
+        }
+        if (!chain) {
+            if (j.distinct) {  // PAPER: every passing trigger triplet is a candidate
+                const bool f = nT >= 2 && block_disjoint_pair<kHThreads>(ijk, nullptr, nT, &sm.s_hx);
+                if (tid == 0) j.dpair[e] = f;
+            }
+            break;
         }
         if (tid == 0) sm.s_pool = nT > 0 ? atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nT) : 0ull;
         __syncthreads();
@@ -1362,6 +1427,7 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
             for (int i = tid; i < nT; i += kHThreads) {
                 j.tpool[pb + i] = T[i];
                 j.tpool_alive[pb + i] = 1;
+                if (ijk) j.tpool_ijk[pb + i] = ijk[i];
             }
             if (tid == 0) j.hT[gi] = make_int2((int)pb, nT);
             return;
@@ -1379,6 +1445,10 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
         if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
         __syncthreads();
         tc = sm.s_cand;
+        if (j.distinct) {
+            const bool f = nT >= 2 && block_disjoint_pair<kHThreads>(ijk, alive, nT, &sm.s_hx);
+            if (tid == 0) j.dpair[e] = f;
+        }
     }
     if (tid == 0) {
         if (j.mode == 0)
@@ -1397,6 +1467,7 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
 struct MediumSmem {
     BlockSmem<MedBCfg> b;
     float2 T[kTCap];
+    unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
     uint8_t alive[kTCap];
 };
 
@@ -1425,19 +1496,20 @@ __device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_
         const int s = station_of(si, j.trig);
         if (tid == 0) sm.s_nT = 0;
         __syncthreads();
-        TSink ts{chain && si == 0, ms.T, kTCap, &sm.s_nT, 0};
+        TSink ts{(chain || j.distinct) && si == 0, ms.T, kTCap, &sm.s_nT, 0};
+        ts.ijk = j.distinct ? ms.Tijk : nullptr;
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
         if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt, sn)) return;
         __syncthreads();
         if (si > 0) continue;
         trig_count = cnt;
-        if (!chain) break;
         nT = sm.s_nT;
         if (nT > kTCap) {  // more trigger slopes than this tile keeps
             if (tid == 0) push_event(j, e, kClsHeavy);
             return;
         }
+        if (!chain) break;
         for (int i = tid; i < nT; i += MedBCfg::THREADS) ms.alive[i] = 1;
         __syncthreads();
     }
@@ -1451,6 +1523,11 @@ __device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_
         if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
         __syncthreads();
         tc = sm.s_cand;
+    }
+    if (j.distinct) {
+        const bool f = nT >= 2 && block_disjoint_pair<MedBCfg::THREADS>(ms.Tijk, chain ? ms.alive : nullptr, nT,
+                                                                         &sm.s_hx);
+        if (tid == 0) j.dpair[e] = f;
     }
     if (tid == 0) {
         if (j.mode == 0)
@@ -1608,6 +1685,10 @@ __global__ void k_heavy_final(const __grid_constant__ Job j) {
         for (int t = lane; t < h.y; t += 32) a += j.tpool_alive[h.x + t];
         a = __reduce_add_sync(kFull, a);
         if (lane == 0) j.track_counts[e] = a;
+        if (j.distinct) {
+            const bool f = a >= 2 && warp_disjoint_pair(j.tpool_ijk + h.x, j.tpool_alive + h.x, h.y, lane);
+            if (lane == 0) j.dpair[e] = f;
+        }
     }
 }
 
@@ -1660,7 +1741,43 @@ struct GenShared {
     int* s_count;
     int* s_cand;
     int* s_bad;
+    unsigned long long* s_pool;
 };
+
+constexpr int kGenThreads = 256;  // block size of the unpruned search (both callers)
+
+// distinct_hits on the unpruned path: a second pass over the trigger
+// station writes the packed hits of the event's candidates (passing
+// triplets; in CHAIN mode those with a compatible triplet in every other
+// station) to out[0, cap), ranked by the block-shared counter.
+__device__ void generic_candidates(const Job& j, const int32_t* soff, const Cuts& c, unsigned long long* out, int cap,
+                                   int* s_rank) {
+    const int32_t* o = soff + 3 * j.trig;
+    const bool chain = j.mode == 1 && j.S > 1;
+    const int64_t n0 = o[1] - o[0], n1 = o[2] - o[1], n2 = o[3] - o[2];
+    const int64_t npairs = n0 * n1;
+    for (int64_t p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int64_t i = p / n1, jx = p - i * n1;
+        const GHit hi = ghit(j, o[0] + i), hj = ghit(j, o[1] + jx);
+        if (!hi.p.live || !hj.p.live) continue;
+        if (!hi.p.wild && !hj.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hj.p.sx, hj.p.sy, __fadd_rn(hi.p.b, hj.p.b)))
+            continue;
+        for (int64_t k = 0; k < n2; ++k) {
+            const GHit hk = ghit(j, o[2] + k);
+            if (!hk.p.live) continue;
+            if (!hk.p.wild) {
+                if (!hi.p.wild && !pair_ok(hi.p.sx, hi.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hi.p.b, hk.p.b))) continue;
+                if (!hj.p.wild && !pair_ok(hj.p.sx, hj.p.sy, hk.p.sx, hk.p.sy, __fadd_rn(hj.p.b, hk.p.b))) continue;
+            }
+            const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
+            float mx, my;
+            if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
+            if (chain && !road_global(j, soff, c, mx, my)) continue;
+            const int r = atomicAdd(s_rank, 1);
+            if (r < cap) out[r] = pack_ijk((int)i, (int)jx, (int)k);
+        }
+    }
+}
 
 // The unpruned search of one event by one block: any size, any coordinates
 // (pruning only where the per-hit bound is finite).  Counting pass: unit
@@ -1773,14 +1890,36 @@ __device__ void generic_event(const Job& j, int64_t e, const GenShared& g) {
                 if (s != j.trig) j.unit_counts[e * S + s] = 0;
         j.track_counts[e] = chain ? *g.s_cand : trig_count;
     }
+    if (!EMIT && !bad_event && j.distinct) {  // block-uniform
+        const int nc = chain ? *g.s_cand : trig_count;
+        bool f = false;
+        if (nc >= 2) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                *g.s_pool = atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nc);
+                *g.s_count = 0;
+            }
+            __syncthreads();
+            const unsigned long long pb = *g.s_pool;
+            if (pb + (unsigned long long)nc <= (unsigned long long)j.tpool_cap) {
+                generic_candidates(j, soff, c, j.tpool_ijk + pb, nc, g.s_count);
+                __syncthreads();
+                f = block_disjoint_pair<kGenThreads>(j.tpool_ijk + pb, nullptr, nc, g.s_bad);
+            } else if (threadIdx.x == 0) {
+                atomicOr(&j.ctrl->status, kStNoPool);
+            }
+        }
+        if (threadIdx.x == 0) j.dpair[e] = f;
+    }
     __syncthreads();
 }
 
 // Persistent blocks take the events of the unpruned list.
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_generic(const __grid_constant__ Job j) {
+__global__ void __launch_bounds__(kGenThreads) k_generic(const __grid_constant__ Job j) {
     __shared__ int32_t soff[3 * kMaxStations + 1];
     __shared__ int s_gi, s_count, s_cand, s_bad;
+    __shared__ unsigned long long s_pool;
     const int n_gen = *(volatile int32_t*)&j.ctrl->n_generic, g0 = *(volatile int32_t*)&j.ctrl->g_begin;
     for (;;) {
         if (threadIdx.x == 0) s_gi = g0 + (int)atomicAdd(&j.ctrl->work[EMIT ? 7 : 3], 1ull);
@@ -1788,7 +1927,8 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ Job j) 
         const int gi = s_gi;
         if (gi >= n_gen) break;
         const int64_t e = j.glist[gi];
-        if (!EMIT || j.ev_class[e] == kClsGeneric) generic_event<EMIT>(j, e, GenShared{soff, &s_count, &s_cand, &s_bad});
+        if (!EMIT || j.ev_class[e] == kClsGeneric)
+            generic_event<EMIT>(j, e, GenShared{soff, &s_count, &s_cand, &s_bad, &s_pool});
         __syncthreads();
     }
 }
@@ -1844,12 +1984,13 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
     }
     float2* T = ps.T;
     uint8_t* alive = ps.alive;
+    unsigned long long* ijk = nullptr;  // distinct_hits: the candidates' packed hits (in the pool)
     int trig_count = 0, nT = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
         if (tid == 0) sm.s_nT = 0;
         __syncthreads();
-        TSink ts{chain && si == 0, T, kPlainTCap, &sm.s_nT, 0};
+        TSink ts{(chain || j.distinct) && si == 0, T, kPlainTCap, &sm.s_nT, 0};
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
         if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) {
@@ -1859,11 +2000,12 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         __syncthreads();
         if (si > 0) continue;
         trig_count = cnt;
-        if (!chain) break;
+        if (!chain && !j.distinct) break;
         nT = sm.s_nT;
-        if (nT > kPlainTCap) {
-            // more slopes than the block keeps: room in the batch's pool, and
-            // the trigger station once more (same count, nothing recorded)
+        if (nT > kPlainTCap || (j.distinct && nT >= 2)) {
+            // more slopes than the block keeps, or (distinct_hits) the
+            // candidates' hits wanted: room in the batch's pool, and the
+            // trigger station once more (same count, nothing recorded)
             if (tid == 0) sm.s_pool = atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nT);
             __syncthreads();
             const unsigned long long pb = sm.s_pool;
@@ -1873,15 +2015,22 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
             }
             T = j.tpool + pb;
             alive = j.tpool_alive + pb;
+            if (j.distinct) ijk = j.tpool_ijk + pb;
             if (tid == 0) sm.s_nT = 0;
             __syncthreads();
             TSink ts2{true, T, nT, &sm.s_nT, 0};
             ts2.norec = true;
+            ts2.ijk = ijk;
             if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts2, nullptr, nullptr, 0, cnt)) {
                 __syncthreads();
                 return j.ev_class[e] == kClsGeneric;
             }
             __syncthreads();
+        }
+        if (!chain) {  // PAPER with distinct_hits: every passing trigger triplet is a candidate
+            const bool f = nT >= 2 && block_disjoint_pair<kHThreads>(ijk, nullptr, nT, &sm.s_hx);
+            if (tid == 0) j.dpair[e] = f;
+            break;
         }
         for (int i = tid; i < nT; i += kHThreads) alive[i] = 1;
         __syncthreads();
@@ -1896,6 +2045,10 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         if (lane == 0 && a) atomicAdd(&sm.s_cand, a);
         __syncthreads();
         tc = sm.s_cand;
+        if (j.distinct) {
+            const bool f = nT >= 2 && block_disjoint_pair<kHThreads>(ijk, alive, nT, &sm.s_hx);
+            if (tid == 0) j.dpair[e] = f;
+        }
     }
     if (tid == 0) {
         if (j.mode == 0)
@@ -1915,7 +2068,7 @@ __global__ void __launch_bounds__(kHThreads, 3) k_plain_block(const __grid_const
     const uint8_t cls = j.ev_class[e];
     bool generic = cls == kClsGeneric;
     if (cls == kClsHeavy) generic = plain_block_event<EMIT>(j, ps, e);
-    if (generic) generic_event<EMIT>(j, e, GenShared{ps.h.off, &ps.h.s_rank, &ps.h.s_cand, &ps.h.s_next});
+    if (generic) generic_event<EMIT>(j, e, GenShared{ps.h.off, &ps.h.s_rank, &ps.h.s_cand, &ps.h.s_next, &ps.h.s_pool});
 }
 
 // -------------------------------------------------------- accept bits
@@ -1927,7 +2080,8 @@ __global__ void k_accept(const __grid_constant__ Job j) {
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwords; w += wstride) {
         const int64_t e = w * 32 + lane;
-        const bool v = e < j.n_events && j.track_counts[e] >= j.minc;
+        // distinct_hits with min_candidates 2: two candidates sharing no hit
+        const bool v = e < j.n_events && (j.distinct && j.minc == 2 ? j.dpair[e] != 0 : j.track_counts[e] >= j.minc);
         const unsigned bits = __ballot_sync(kFull, v);
         if (lane == 0) j.accept_bits[w] = bits;
     }
@@ -2178,7 +2332,7 @@ cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t s
     k_heavy<<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_heavy_units<false><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
     k_heavy_final<<<lc.scan_blocks, 256, 0, st>>>(j);
-    k_generic<false><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
+    k_generic<false><<<lc.generic_blocks, kGenThreads, 0, st>>>(j);
     return cudaGetLastError();
 }
 
@@ -2261,7 +2415,7 @@ cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg&
     k_light<true><<<(unsigned)nb, wpb * 32, smem, st>>>(j);
     k_medium<true><<<lc.medium_blocks, MedBCfg::THREADS, medium_smem_bytes(), st>>>(j);
     k_heavy_units<true><<<lc.heavy_blocks, kHThreads, heavy_smem_bytes(), st>>>(j);
-    k_generic<true><<<lc.generic_blocks, lc.generic_threads, 0, st>>>(j);
+    k_generic<true><<<lc.generic_blocks, kGenThreads, 0, st>>>(j);
     return cudaGetLastError();
 }
 
@@ -2315,8 +2469,8 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     if (p->n_stations < 1 || p->n_stations > kMaxStations || p->trigger_station < 0 ||
         p->trigger_station >= p->n_stations || (p->mode != JPSI_MODE_PAPER && p->mode != JPSI_MODE_CHAIN) ||
         p->ndf < 1 || p->min_candidates < 0 || !(p->t_xz >= 0.0f) || !(p->t_yz >= 0.0f) ||
-        std::isinf(p->t_xz) || std::isinf(p->t_yz))
-        return JPSI_EINVAL;
+        std::isinf(p->t_xz) || std::isinf(p->t_yz) || p->distinct_hits != 0)
+        return JPSI_EINVAL;  // (distinct_hits changes accept bits only, which this entry point does not return)
     if (b->n_events < 0 || b->n_events > kNoAllocMaxEvents) return JPSI_EINVAL;  // beyond the static scratch
     if (b->n_hits < 0 || b->n_hits >= ((int64_t)1 << 31) || (b->n_events == 0 && b->n_hits != 0)) return JPSI_EINVAL;
     if (b->n_events == 0) return JPSI_OK;

@@ -61,3 +61,18 @@ def sorted_triplets(trip_off, triplets, n_units):
 def accept_list(bits, n_events):
     v = np.unpackbits(np.asarray(bits, np.uint32).view(np.uint8), bitorder="little")
     return v[:n_events].astype(bool)
+
+
+def shared_hit_event(n_stations, third, dz=10.0, pitch=35.0, z0=120.0):
+    """Every station: two close tracks in layers 0 and 2 and one middle-layer
+    hit between them, so the trigger station's passing triplets all use that
+    hit; `third` adds a separate track through every layer."""
+    ev = []
+    for s in range(n_stations):
+        for l in range(3):
+            z = z0 + pitch * s + dz * (l - 1)
+            hits = [(0.1 * z + 0.4, 0.1 * z, z)] if l == 1 else [(0.1 * z, 0.1 * z, z), (0.1 * z + 0.8, 0.1 * z, z)]
+            if third:
+                hits.append((-0.2 * z, 0.15 * z, z))
+            ev.append(hits)
+    return ev

@@ -448,3 +448,57 @@ def test_ndf_and_min_candidates(lib, oracle_mod, synth_mod, ndf, minc, cuts):
             for form in ("plain", "batched"):
                 assert_same(gpu_select(ctx, b, form=form), ref, n * 4, label=f"{wl} mode={mode} {form}")
             ctx.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_distinct_hits(lib, oracle_mod, synth_mod, mode):
+    # "at least two triplets" (Sec. 3.2 step 3) read as two candidates that
+    # share no hit, on every path: small and medium tiles (Poisson(20),
+    # log-normal), the block tile (dense trigger stations, split by station in
+    # CHAIN mode), the unpruned kernel (a layer past the block tile) and hand
+    # events whose candidates all share the middle-layer hit
+    from helpers import shared_hit_event
+    rng = np.random.default_rng(77)
+    dense = []
+    for _ in range(8):
+        tx, ty = rng.uniform(-0.3, 0.3, 2)
+        dense.append([[(tx * z + rng.normal(0, 0.05), ty * z + rng.normal(0, 0.05), z) for _ in range(9)]
+                      for z in (120.0, 130.0, 140.0, 155.0, 165.0, 175.0)])
+    huge = []
+    for n in (2100, 2200):
+        ev = []
+        for li, z in enumerate((120.0, 130.0, 140.0, 155.0, 165.0, 175.0)):
+            m = n if li == 4 else 30
+            r = rng.uniform(15, 0.4 * z, m)
+            ph = rng.uniform(0, 2 * np.pi, m)
+            hits = [(float(a * np.cos(p)), float(a * np.sin(p)), z) for a, p in zip(r, ph)]
+            hits += [(0.1 * z + 0.3 * q, -0.05 * z, z) for q in range(3)]
+            ev.append(hits)
+        huge.append(ev)
+    shared = [shared_hit_event(2, False, dz=10.0, pitch=35.0) for _ in range(3)] + [shared_hit_event(2, True)]
+    cases = [("poisson20_1k", synth_mod.generate("poisson20_1k", 0, 1000), 4, 0.25),
+             ("lognormal", synth_mod.generate("lognormal_timeslices", 0, 2000), 4, 0.25),
+             ("dense+huge+shared", make_batch(dense + huge + shared, 2), 2, 0.25)]
+    for name, b, S, t in cases:
+        ref = oracle_mod.run(oracle_mod.params(S, mode, t_xz=t, distinct_hits=1), b, n_threads=16)
+        base = oracle_mod.run(oracle_mod.params(S, mode, t_xz=t), b, n_threads=16)
+        assert ref["status"] == 0
+        if name.startswith("dense"):  # the rule decides some events here
+            assert not np.array_equal(ref["accept_bits"], base["accept_bits"])
+        ctx = lib.Context(lib.params(S, mode, t_xz=t, distinct_hits=1))
+        for form in ("plain", "batched"):
+            assert_same(gpu_select(ctx, b, form=form), ref, b["n_events"] * S, label=f"{name} mode={mode} {form}")
+        ctx.close()
+
+
+def test_distinct_hits_parameters(lib):
+    import ctypes
+    for minc, ok in ((0, True), (1, True), (2, True), (3, False)):
+        p = lib.params(4, 1, min_candidates=minc, distinct_hits=1)
+        if ok:
+            lib.Context(p).close()
+        else:
+            with pytest.raises(lib.JpsiError):
+                lib.Context(p)
+    with pytest.raises(lib.JpsiError):
+        lib.Context(lib.params(4, 1, distinct_hits=2))

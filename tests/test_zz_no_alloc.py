@@ -58,6 +58,10 @@ def test_noalloc_matches_regular_entry_point(lib, synth_mod, mode):
 def test_noalloc_rejects_batches_beyond_its_limits(lib, synth_mod):
     import torch
     p = lib.params(4, 1, t_xz=0.25)
+    # the hit-disjoint accept rule changes accept bits only, which this entry
+    # point does not return: refused
+    nb = lib.jpsi_batch()
+    assert lib.jpsi_select_noalloc(lib.params(4, 1, t_xz=0.25, distinct_hits=1), nb, None, None, 0) == lib.JPSI_EINVAL
     # more events than the fixed scratch holds: refused before anything runs
     big = lib.jpsi_batch()
     big.n_events, big.n_hits = (1 << 18) + 1, 0
