@@ -36,6 +36,10 @@ class Params(ctypes.Structure):
     ]
 
 
+class Stream(ctypes.Structure):
+    _fields_ = [("n_windows", ctypes.c_int32), ("dt", ctypes.c_float), ("bounds", ctypes.c_void_p)]
+
+
 def params(n_stations=4, mode=MODE_CHAIN, t_xz=0.25, t_yz=None, ndf=2, min_candidates=2, trigger_station=None,
            distinct_hits=0):
     p = Params()
@@ -80,6 +84,9 @@ def _load():
         lib.jpsi_oracle_triplet64.restype = ctypes.c_int
         lib.jpsi_oracle_cut.argtypes = [ctypes.c_int32, ctypes.c_float]
         lib.jpsi_oracle_cut.restype = ctypes.c_float
+        lib.jpsi_oracle_stream.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Stream), ctypes.c_int64, vp, vp, vp,
+                                           vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp]
+        lib.jpsi_oracle_stream.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -143,4 +150,36 @@ def run(p: Params, batch, *, triplets=True, capacity=None, n_threads=1, brute=Fa
         res["triplets"] = trip[: needed.value]
     else:
         res["triplets"] = None
+    return res
+
+
+def stream(p: Params, ts, bounds, dt, *, triplets=True):
+    """The free-streaming selection over one timeslice (dict with x, y, z, t
+    and offsets [n_stations*3 + 1], each layer group sorted by t): windows
+    [bounds[k], bounds[k+1]), coincidence width dt.  Returns the dict of
+    run() with windows in place of events."""
+    lib = _load()
+    S = p.n_stations
+    b = np.ascontiguousarray(bounds, dtype=np.float32)
+    K = len(b) - 1
+    x, y, z, t = (np.ascontiguousarray(ts[k], dtype=np.float32) for k in ("x", "y", "z", "t"))
+    off = np.ascontiguousarray(ts["offsets"], dtype=np.int32)
+    sp = Stream(K, dt, b.ctypes.data)
+    acc = np.zeros((K + 31) // 32, np.uint32)
+    tc = np.zeros(K, np.int32)
+    uc = np.zeros(K * S, np.int32)
+    to = np.zeros(K * S + 1, np.int64)
+    needed = ctypes.c_int64(-1)
+    args = [ctypes.byref(p), ctypes.byref(sp), x.size, x.ctypes.data, y.ctypes.data, z.ctypes.data, t.ctypes.data,
+            off.ctypes.data]
+    rc = lib.jpsi_oracle_stream(*args, acc.ctypes.data, tc.ctypes.data, to.ctypes.data, None, 0,
+                                ctypes.byref(needed), uc.ctypes.data)
+    res = {"status": rc, "accept_bits": acc, "track_counts": tc, "unit_counts": uc, "trip_off": to,
+           "trip_needed": needed.value, "triplets": None}
+    if rc == OK and triplets:
+        trip = np.zeros((max(needed.value, 1), 3), np.int32)
+        rc = lib.jpsi_oracle_stream(*args, acc.ctypes.data, tc.ctypes.data, to.ctypes.data, trip.ctypes.data,
+                                    needed.value, ctypes.byref(needed), uc.ctypes.data)
+        res["status"] = rc
+        res["triplets"] = trip[: needed.value]
     return res

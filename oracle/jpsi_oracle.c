@@ -462,3 +462,177 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
     if (!track_counts) free(tc);
     return rc;
 }
+
+/* ------------------------------------------- free-streaming timeslices */
+/* See jpsi_oracle.h: hits carry times, windows replace events, a triplet
+ * must be coincident (max t <= fl32(min t + dt)) and belongs to the window
+ * of its earliest hit.  Written for clarity: binary searches give each
+ * layer's time range, then every triple in the ranges is tested. */
+
+/* First index i in [lo, hi) with t[i] >= v (t sorted). */
+static int64_t t_lower(const float *t, int64_t lo, int64_t hi, float v) {
+    while (lo < hi) {
+        const int64_t m = lo + (hi - lo) / 2;
+        if (t[m] < v) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
+/* First index i in [lo, hi) with t[i] > v. */
+static int64_t t_upper(const float *t, int64_t lo, int64_t hi, float v) {
+    while (lo < hi) {
+        const int64_t m = lo + (hi - lo) / 2;
+        if (t[m] <= v) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
+typedef struct {
+    int32_t i, j, k;       /* indices within the layer groups */
+    int64_t hi, hj, hk;    /* timeslice hit indices */
+    float mx, my;          /* fitted slopes */
+    float tmin, tmax;      /* earliest and latest hit time */
+} strip_t;
+
+typedef struct {
+    strip_t *v;
+    int64_t n, cap;
+} stripvec;
+
+static int sv_push(stripvec *sv, const strip_t *e) {
+    if (sv->n == sv->cap) {
+        const int64_t nc = sv->cap ? sv->cap * 2 : 64;
+        strip_t *nv = (strip_t *)realloc(sv->v, (size_t)nc * sizeof(strip_t));
+        if (!nv) return 0;
+        sv->v = nv;
+        sv->cap = nc;
+    }
+    sv->v[sv->n++] = *e;
+    return 1;
+}
+
+/* Coincident passing triplets of station s with every hit time in [lo, hi];
+ * when own_end is not NULL only those with earliest time < *own_end. */
+static int stream_station(const jo_params *p, const float *x, const float *y, const float *z, const float *t,
+                          const int32_t *off, float dt, int s, float lo, float hi, const float *own_end,
+                          stripvec *out) {
+    const float cx = jpsi_oracle_cut(p->ndf, p->t_xz), cy = jpsi_oracle_cut(p->ndf, p->t_yz);
+    int64_t a[3], b[3];
+    out->n = 0;
+    for (int l = 0; l < 3; ++l) {
+        a[l] = t_lower(t, off[3 * s + l], off[3 * s + l + 1], lo);
+        b[l] = t_upper(t, a[l], off[3 * s + l + 1], hi);
+        if (a[l] >= b[l]) return JO_OK;
+    }
+    for (int64_t h0 = a[0]; h0 < b[0]; ++h0)
+        for (int64_t h1 = a[1]; h1 < b[1]; ++h1)
+            for (int64_t h2 = a[2]; h2 < b[2]; ++h2) {
+                const float t0 = t[h0], t1 = t[h1], t2 = t[h2];
+                const float tmin = fminf(fminf(t0, t1), t2), tmax = fmaxf(fmaxf(t0, t1), t2);
+                if (!(tmax <= tmin + dt)) continue; /* not coincident */
+                if (own_end && !(tmin < *own_end)) continue; /* earliest hit in a later window */
+                const float xs[3] = {x[h0], x[h1], x[h2]};
+                const float ys[3] = {y[h0], y[h1], y[h2]};
+                const float zs[3] = {z[h0], z[h1], z[h2]};
+                strip_t e;
+                if (!jpsi_oracle_triplet(xs, ys, zs, cx, cy, &e.mx, &e.my, NULL, NULL)) continue;
+                e.i = (int32_t)(h0 - off[3 * s]);
+                e.j = (int32_t)(h1 - off[3 * s + 1]);
+                e.k = (int32_t)(h2 - off[3 * s + 2]);
+                e.hi = h0; e.hj = h1; e.hk = h2;
+                e.tmin = tmin; e.tmax = tmax;
+                if (!sv_push(out, &e)) return JO_ENOMEM;
+            }
+    return JO_OK;
+}
+
+int jpsi_oracle_stream(const jo_params *p, const jo_stream *sp, int64_t n_hits, const float *x, const float *y,
+                       const float *z, const float *t, const int32_t *offsets, uint32_t *accept_bits,
+                       int32_t *track_counts, int64_t *trip_off, int32_t *triplets, int64_t trip_capacity,
+                       int64_t *trip_needed, int32_t *unit_counts) {
+    if (!params_ok(p) || p->distinct_hits || !sp || sp->n_windows < 0 || !(sp->dt >= 0.0f) || isinf(sp->dt))
+        return JO_EINVAL;
+    const int S = p->n_stations, K = sp->n_windows, trig = p->trigger_station;
+    const int chain = p->mode == JO_MODE_CHAIN && S > 1;
+    if (n_hits < 0 || n_hits >= ((int64_t)1 << 31) || !offsets) return JO_EINVAL;
+    if (n_hits > 0 && (!x || !y || !z || !t)) return JO_EINVAL;
+    if (K > 0 && !sp->bounds) return JO_EINVAL;
+    for (int k = 0; k <= K && K > 0; ++k) {
+        if (isnan(sp->bounds[k]) || isinf(sp->bounds[k])) return JO_EINVAL;
+        if (k > 0 && !(sp->bounds[k] > sp->bounds[k - 1])) return JO_EINVAL;
+    }
+    if (offsets[0] != 0 || offsets[3 * S] != n_hits) return JO_EINVAL;
+    for (int g = 0; g < 3 * S; ++g) {
+        if (offsets[g + 1] < offsets[g]) return JO_EINVAL;
+        for (int64_t h = offsets[g]; h < offsets[g + 1]; ++h) {
+            if (isnan(t[h]) || (h > offsets[g] && !(t[h] >= t[h - 1]))) return JO_EINVAL; /* sorted, no NaN */
+            const int s = g / 3;
+            if ((p->mode == JO_MODE_CHAIN || s == trig) && z[h] <= 0.0f) return JO_EINVAL;
+        }
+    }
+    const float cx = jpsi_oracle_cut(p->ndf, p->t_xz), cy = jpsi_oracle_cut(p->ndf, p->t_yz);
+    stripvec per[JO_MAX_STATIONS], other;
+    memset(per, 0, sizeof(per));
+    memset(&other, 0, sizeof(other));
+    int rc = JO_OK;
+    int64_t total = 0, pos = 0;
+    if (trip_off) trip_off[0] = 0;
+    if (accept_bits) memset(accept_bits, 0, (size_t)((K + 31) / 32) * sizeof(uint32_t));
+    for (int k = 0; k < K && rc == JO_OK; ++k) {
+        const float lo = sp->bounds[k], own_end = sp->bounds[k + 1], hi = sp->bounds[k + 1] + sp->dt;
+        for (int s = 0; s < S && rc == JO_OK; ++s) {
+            per[s].n = 0;
+            if (p->mode == JO_MODE_PAPER && s != trig) continue;
+            rc = stream_station(p, x, y, z, t, offsets, sp->dt, s, lo, hi, &own_end, &per[s]);
+        }
+        if (rc != JO_OK) break;
+        int64_t n_cand = 0;
+        for (int64_t a = 0; a < per[trig].n && rc == JO_OK; ++a) {
+            const strip_t *T = &per[trig].v[a];
+            int ok = 1;
+            for (int s = 0; s < S && ok && chain; ++s) {
+                if (s == trig) continue;
+                /* hits of a coincident partner lie in [max_T - dt, fl32(min_T + dt)]
+                 * (searched with a margin below: the exact tests decide) */
+                double lod = (double)T->tmax - (double)sp->dt;
+                lod -= 1e-6 * (fabs((double)T->tmax) + (double)sp->dt) + 1e-30;
+                const float lo_s = nextafterf((float)lod, -INFINITY), hi_s = T->tmin + sp->dt;
+                rc = stream_station(p, x, y, z, t, offsets, sp->dt, s, lo_s, hi_s, NULL, &other);
+                if (rc != JO_OK) break;
+                int found = 0;
+                for (int64_t b2 = 0; b2 < other.n && !found; ++b2) {
+                    const strip_t *u = &other.v[b2];
+                    const float mn = fminf(T->tmin, u->tmin), mx = fmaxf(T->tmax, u->tmax);
+                    if (!(mx <= mn + sp->dt)) continue; /* the six hits not coincident */
+                    const float xs[3] = {x[u->hi], x[u->hj], x[u->hk]};
+                    const float ys[3] = {y[u->hi], y[u->hj], y[u->hk]};
+                    const float zs[3] = {z[u->hi], z[u->hj], z[u->hk]};
+                    found = (chain_plane32(xs, zs, T->mx) <= cx) && (chain_plane32(ys, zs, T->my) <= cy);
+                }
+                ok = found;
+            }
+            n_cand += ok;
+        }
+        if (rc != JO_OK) break;
+        if (track_counts) track_counts[k] = n_cand > INT32_MAX ? INT32_MAX : (int32_t)n_cand;
+        if (accept_bits && n_cand >= p->min_candidates) accept_bits[k >> 5] |= 1u << (k & 31);
+        for (int s = 0; s < S; ++s) {
+            if (unit_counts) unit_counts[(int64_t)k * S + s] = (int32_t)per[s].n;
+            total += per[s].n;
+            if (trip_off) trip_off[(int64_t)k * S + s + 1] = total;
+            if (triplets && total <= trip_capacity)
+                for (int64_t b2 = 0; b2 < per[s].n; ++b2) {
+                    triplets[3 * pos] = per[s].v[b2].i;
+                    triplets[3 * pos + 1] = per[s].v[b2].j;
+                    triplets[3 * pos + 2] = per[s].v[b2].k;
+                    ++pos;
+                }
+        }
+    }
+    for (int s = 0; s < JO_MAX_STATIONS; ++s) free(per[s].v);
+    free(other.v);
+    if (rc != JO_OK) return rc;
+    if (trip_needed) *trip_needed = total;
+    if (triplets && total > trip_capacity) return JO_ECAPACITY;
+    return JO_OK;
+}

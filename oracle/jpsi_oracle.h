@@ -54,6 +54,34 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
                     int64_t *trip_off, int32_t *triplets, int64_t trip_capacity, int64_t *trip_needed,
                     int32_t *unit_counts, int n_threads, int brute, int fp64);
 
+/*
+ * Free-streaming selection (an extension; the paper's Outlook, Sec. 8, only
+ * says that free-streaming data need hit times and event building).  One
+ * timeslice of hits with times t (ns, float32), grouped per (station, layer):
+ * offsets [n_stations*3 + 1], each group sorted by t (non-decreasing, no
+ * NaN).  Windows k = 0 .. n_windows-1 are [bounds[k], bounds[k+1]) (bounds
+ * strictly increasing, finite).  A triplet (one hit per layer of a station)
+ * is coincident when max t <= fl32(min t + dt); it belongs to the window
+ * that holds its earliest time.  Passing triplets of window k at station s
+ * are its coincident triplets that pass P1; in CHAIN mode a passing trigger
+ * triplet T of window k is a candidate when every other station holds a
+ * passing coincident triplet t (of any window) compatible with T (P2) whose
+ * six hits together are coincident.  Window k is accepted when it holds at
+ * least min_candidates candidates.  Outputs as for jpsi_oracle_run with
+ * windows in place of events; triplet rows are indices into the timeslice's
+ * layer groups.  distinct_hits must be 0.
+ */
+typedef struct {
+    int32_t n_windows;
+    float dt;             /* coincidence width, ns, >= 0 */
+    const float *bounds;  /* [n_windows + 1] window starts and the last end */
+} jo_stream;
+
+int jpsi_oracle_stream(const jo_params *p, const jo_stream *sp, int64_t n_hits, const float *x, const float *y,
+                       const float *z, const float *t, const int32_t *offsets, uint32_t *accept_bits,
+                       int32_t *track_counts, int64_t *trip_off, int32_t *triplets, int64_t trip_capacity,
+                       int64_t *trip_needed, int32_t *unit_counts);
+
 /* P1 on one triplet (hits k = 0,1,2 from layers 0,1,2): returns 1 if it
  * passes both planes; writes the fitted slopes. */
 int jpsi_oracle_triplet(const float xs[3], const float ys[3], const float zs[3], float c_xz, float c_yz,
