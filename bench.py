@@ -348,7 +348,9 @@ def run_serving(args, w, dev, jp, torch):
     slot_hits = max(q["hits"] for q in pool)
     slot_trip = max(q["trip"] for q in pool)
     ctx.check(jp.jpsi_serve_start(ctx.ctx, args.slots, slot_events, slot_hits, slot_trip))
-    ring_n = 2 * args.slots + 2
+    # enough output buffers that buffer reuse never holds a submission back
+    # behind a slow earlier request (a short ring coupled the requests)
+    ring_n = max(64, 4 * args.slots)
     ring = []
     for _ in range(ring_n):
         ob = {"acc": torch.empty((slot_events + 31) // 32, dtype=torch.int32, pin_memory=True),
@@ -423,7 +425,9 @@ def run_serving(args, w, dev, jp, torch):
         return out
 
     run_load(None, False)  # warm-up: graphs, buffers
+    jp.jpsi_timing_enable(ctx.ctx, True)
     sat = run_load(None, True)
+    tm = jp.jpsi_timing_get(ctx.ctx)
     cap = sat["sustained_events_per_s"]
     loads = [run_load(w.extra["rate_events_per_s"], True)]
     for f in (0.5, 0.8, 0.95):
@@ -437,6 +441,7 @@ def run_serving(args, w, dev, jp, torch):
                        "events_per_load": n_events, "slots": args.slots, "slot_events": slot_events,
                        "slot_hits": slot_hits, "hbm_budget_gb": args.serve_budget_gb, "mode": args.mode},
             "saturation": sat, "loads": loads,
+            "kernel_launches_per_request": tm.kernel_launches / max(tm.runs, 1),
             "isolation": all(r.get("results_equal_solo", True) for r in [sat] + loads),
             "generate_s": gen_s}
     if not args.no_cpu_baseline:

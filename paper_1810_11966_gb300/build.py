@@ -13,6 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjpsi.so")
 SOURCES = ["jpsi_kernels.cu", "jpsi_api.cu"]
+# jpsi_kernels.cu once more with the time tests of free-streaming windows
+STREAM_UNIT = ("jpsi_kernels.cu", "jpsi_kernels_stream.o", ["-DJPSI_STREAM=1"])
 HEADERS = ["jpsi_device.cuh", "jpsi_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xptxas", "-v", "-Xcompiler", "-fPIC,-O2",
@@ -40,18 +42,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj_name, extra = unit
+        obj = os.path.join(BUILD, obj_name)
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
-        with open(os.path.join(BUILD, src + ".log"), "w") as f:
+        with open(os.path.join(BUILD, obj_name.replace(".o", ".log")), "w") as f:
             f.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr[-6000:]}")
+            raise RuntimeError(f"nvcc failed on {src} {extra}:\n{r.stderr[-6000:]}")
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES] + [STREAM_UNIT]
+    with ThreadPoolExecutor(len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.replace(tmp, LIB)
     if verbose:
         for src in SOURCES:
-            print(open(os.path.join(BUILD, src + ".log")).read())
+            print(open(os.path.join(BUILD, src.replace(".cu", ".log"))).read())
     return LIB
 
 

@@ -22,6 +22,7 @@
 #include "jpsi_internal.h"
 
 using namespace jpsi;
+using namespace jpsi::basek;  // the event kernels; stream runs take jpsi::streamk's launchers
 
 namespace {
 
@@ -66,6 +67,7 @@ struct RunState {
     int64_t tscr_want = (int64_t)1 << 22;  // entries; grows after an overflow
     Graph g_light, g_rest, g_emit, g_scatter;
     int g_cfg_id = -1;
+    bool g_stream = false;  // the graphs hold the free-streaming kernels
     cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
     cudaEvent_t chunk_ev[kMaxChunks] = {};  // hit chunks copied (pipelined host run)
 };
@@ -87,6 +89,32 @@ struct Done {
     jpsi_status st;
     double latency;
 };
+
+// The launchers of one build of the kernels: the event kernels or those of
+// free-streaming windows (time tests compiled in).
+struct Launchers {
+    bool stream;
+    decltype(&basek::launch_light_count) light_count;
+    decltype(&basek::launch_count_rest) count_rest;
+    decltype(&basek::launch_emit_phase) emit_phase;
+    decltype(&basek::launch_scatter) scatter;
+    decltype(&basek::launch_plain_light) plain_light;
+    decltype(&basek::launch_plain_rest) plain_rest;
+    decltype(&basek::launch_plain_emit) plain_emit;
+};
+const Launchers kEventL{false, basek::launch_light_count, basek::launch_count_rest, basek::launch_emit_phase,
+                        basek::launch_scatter, basek::launch_plain_light, basek::launch_plain_rest,
+                        basek::launch_plain_emit};
+// Time inputs of a run over free-streaming windows (device pointers).
+struct StreamJob {
+    const float* t;   // [window-batch hits]
+    const float* wb;  // [n_windows + 1]
+    float dt;
+};
+
+const Launchers kStreamL{true, streamk::launch_light_count, streamk::launch_count_rest, streamk::launch_emit_phase,
+                         streamk::launch_scatter, streamk::launch_plain_light, streamk::launch_plain_rest,
+                         streamk::launch_plain_emit};
 
 }  // namespace
 
@@ -377,18 +405,18 @@ void state_free(jpsi_ctx* c, RunState& rs) {
 
 // Captures the count and emit phases of the batched form into graphs (with
 // the current job; graph_launch writes each run's job into their nodes).
-jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
-    if (rs.g_light.exec && rs.g_cfg_id == c->cfg_id) return JPSI_OK;
+jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs, const Launchers& L = kEventL) {
+    if (rs.g_light.exec && rs.g_cfg_id == c->cfg_id && rs.g_stream == L.stream) return JPSI_OK;
     std::lock_guard<std::mutex> cap_lock(c->cap_mu);
     destroy_graphs(rs);
     for (int phase = 0; phase < 4; ++phase) {
         Graph& G = phase == 0 ? rs.g_light : phase == 1 ? rs.g_rest : phase == 2 ? rs.g_emit : rs.g_scatter;
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
-        cudaError_t le = phase == 0   ? launch_light_count(rs.job, 0, c->batch_cfg, true, c->cap_stream)
-                         : phase == 1 ? launch_count_rest(rs.job, c->batch_cfg, c->cap_stream)
-                         : phase == 2 ? launch_emit_phase(rs.job, 0, c->batch_cfg, true, c->cap_stream)
-                                      : launch_scatter(rs.job, c->batch_cfg, c->cap_stream);
+        cudaError_t le = phase == 0   ? L.light_count(rs.job, 0, c->batch_cfg, true, c->cap_stream)
+                         : phase == 1 ? L.count_rest(rs.job, c->batch_cfg, c->cap_stream)
+                         : phase == 2 ? L.emit_phase(rs.job, 0, c->batch_cfg, true, c->cap_stream)
+                                      : L.scatter(rs.job, c->batch_cfg, c->cap_stream);
         e = cudaStreamEndCapture(c->cap_stream, &G.g);
         if (le != cudaSuccess) return cuda_fail(c, le, "graph capture launch");
         if (e != cudaSuccess) return cuda_fail(c, e, "graph end capture");
@@ -408,6 +436,7 @@ jpsi_status capture_graphs(jpsi_ctx* c, RunState& rs) {
         if ((e = cudaGraphInstantiate(&G.exec, G.g, 0)) != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     }
     rs.g_cfg_id = c->cfg_id;
+    rs.g_stream = L.stream;
     return JPSI_OK;
 }
 
@@ -444,7 +473,8 @@ void add_timing(jpsi_ctx* c, RunState& rs, int launches, bool emitted) {
 
 // The common run: count phase, status/capacity check, emit phase.
 jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, cudaStream_t st,
-                       bool batched, bool host_hits = false) {
+                       bool batched, bool host_hits = false, const Launchers& L = kEventL,
+                       const StreamJob* sj = nullptr) {
     jpsi_status s;
     jpsi_batch bz;
     if (!b->z && b->n_hits > 0) {
@@ -458,18 +488,24 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         b = &bz;
     }
     if ((s = prepare(c, rs, b, o, host_hits)) != JPSI_OK) return s;
+    if (sj) {  // free-streaming windows: the time tests' inputs
+        rs.job.stream = 1;
+        rs.job.dt = sj->dt;
+        rs.job.t = sj->t;
+        rs.job.wb = sj->wb;
+    }
     const int64_t ne = b->n_events;
     cudaError_t e;
     if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
     if (c->p.distinct_hits && ne > 0 && (e = cudaMemsetAsync(rs.dpair.p, 0, (size_t)ne, st)) != cudaSuccess)
         return cuda_fail(c, e, "flag reset");
     const bool timing = c->timing.load();
-    if (batched && (s = capture_graphs(c, rs)) != JPSI_OK) return s;
+    if (batched && (s = capture_graphs(c, rs, L)) != JPSI_OK) return s;
     if (timing) cudaEventRecord(rs.ev[0], st);
-    e = batched ? graph_launch(rs.g_light, rs.job, st) : launch_plain_light(rs.job, c->plain_cfg, st);
+    e = batched ? graph_launch(rs.g_light, rs.job, st) : L.plain_light(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "light count");
     if (timing) cudaEventRecord(rs.ev[1], st);
-    e = batched ? graph_launch(rs.g_rest, rs.job, st) : launch_plain_rest(rs.job, c->plain_cfg, st);
+    e = batched ? graph_launch(rs.g_rest, rs.job, st) : L.plain_rest(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "count rest");
     if (timing) cudaEventRecord(rs.ev[2], st);
     int launches = batched ? kLaunchesLight + kLaunchesRest : kLaunchesPlainLight + kLaunchesPlainRest;
@@ -499,9 +535,9 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         rs.tscr_want = std::max<int64_t>(rs.tscr_want, (int64_t)(ctl.scratch_n + ctl.scratch_n / 4));
     if (timing) cudaEventRecord(rs.ev[3], st);
     if (scattered)
-        e = batched ? graph_launch(rs.g_scatter, rs.job, st) : launch_scatter(rs.job, c->plain_cfg, st);
+        e = batched ? graph_launch(rs.g_scatter, rs.job, st) : L.scatter(rs.job, c->plain_cfg, st);
     else
-        e = batched ? graph_launch(rs.g_emit, rs.job, st) : launch_plain_emit(rs.job, c->plain_cfg, st);
+        e = batched ? graph_launch(rs.g_emit, rs.job, st) : L.plain_emit(rs.job, c->plain_cfg, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "emit");
     if (timing) cudaEventRecord(rs.ev[4], st);
     launches += scattered ? kLaunchesScatter : batched ? kLaunchesEmit : kLaunchesPlainEmit;

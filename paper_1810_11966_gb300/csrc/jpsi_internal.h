@@ -76,6 +76,14 @@ struct Job {
     int64_t ev_begin, ev_count;   // events the warp kernels take from the batch (all by default)
     int32_t S, trig, mode, minc;
     int32_t distinct;             // distinct_hits: accept bits from dpair when minc == 2
+    // free-streaming windows (events are time windows built from a
+    // timeslice): a triplet counts when coincident, max t <= fl32(min t + dt),
+    // and owned by its window, wb[e] <= min t < wb[e + 1]; CHAIN partners
+    // must be coincident with the trigger triplet
+    int32_t stream;
+    float dt;
+    const float* t;               // [n_hits] hit times (stream)
+    const float* wb;              // [n_events + 1] window bounds (stream)
     float cx, cy, K;
     int32_t grab;                 // events per atomic grab (persistent light kernel)
     int32_t cap_small, cap_medium;// most hits per layer on the small / medium warp tile (<= the tile's own)
@@ -117,44 +125,53 @@ struct LaunchCfg {
     int scan_blocks = 0;
 };
 
-// Launchers (jpsi_kernels.cu).  All asynchronous on `st`.
-// Count phase = small warp kernel, then the rest (medium warp kernel,
-// block-tile kernels, unpruned block kernel, accept bits, scan).  Kernel
-// launches per call: 1 and 10.
-cudaError_t launch_light_count(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
-                               cudaStream_t st);
-cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-// The rest split in two, for counting a batch chunk by chunk: the medium,
-// block-tile (sort + 3 kernels) and unpruned kernels (6 launches), then
-// accept bits and scan (4).
-cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st);
+// Launchers (jpsi_kernels.cu), declared for both builds of that file: the
+// event kernels (jpsi::basek) and those of free-streaming windows
+// (jpsi::streamk).  All asynchronous on `st`.
+//   launch_light_count, launch_count_rest: the counting phase = the small
+//     warp kernel (1 launch), then the rest (medium tile, block tiles,
+//     unpruned kernel, accept bits, scan: 10 launches).
+//   launch_count_lists, launch_count_tail: the rest split in two, for counting
+//     a batch chunk by chunk (6 + 4 launches).
+//   launch_scatter: the counting pass's triplet entries to trip_off[unit] + rank.
+//   launch_emit_phase: the fallback when the entries overflowed; the
+//     enumeration kernels write rows at trip_off (4 launches).
+//   launch_plain_*: the one-launch form (no lists, queues or graphs): the
+//     static warp grid (1), then the static block grid and the tail (1 + 4);
+//     its emit fallback is the two static grids again (2).
+//   launch_expand_z: per-hit z of events [ev0, ev1) from a per-layer table.
+#define JPSI_DECLARE_LAUNCHERS                                                                                  \
+    cudaError_t launch_light_count(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,    \
+                                   cudaStream_t st);                                                          \
+    cudaError_t launch_count_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);                        \
+    cudaError_t launch_count_lists(const Job& j, const LaunchCfg& lc, cudaStream_t st);                       \
+    cudaError_t launch_count_tail(const Job& j, const LaunchCfg& lc, cudaStream_t st);                        \
+    cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st);                           \
+    cudaError_t launch_emit_phase(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,     \
+                                  cudaStream_t st);                                                           \
+    cudaError_t launch_plain_light(const Job& j, const LaunchCfg& lc, cudaStream_t st);                       \
+    cudaError_t launch_plain_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);                        \
+    cudaError_t launch_plain_emit(const Job& j, const LaunchCfg& lc, cudaStream_t st);                        \
+    cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, int64_t ev0, int64_t ev1, \
+                                int S, int64_t n_hits, int n_sm, cudaStream_t st);                            \
+    size_t light_smem_bytes(int wpb);                                                                         \
+    int light_max_blocks_per_sm(int wpb);                                                                     \
+    int generic_max_blocks_per_sm(int threads);                                                               \
+    int heavy_max_blocks_per_sm();                                                                            \
+    int medium_max_blocks_per_sm();                                                                           \
+    size_t heavy_smem_bytes();                                                                                \
+    const void* light_count_kernel_ptr();
+
+namespace basek {
+JPSI_DECLARE_LAUNCHERS
+}
+namespace streamk {
+JPSI_DECLARE_LAUNCHERS
+}
 constexpr int kLaunchesLight = 1, kLaunchesRest = 10, kLaunchesEmit = 4;
-// Places the counting pass's triplet entries at trip_off[unit] + rank.
-cudaError_t launch_scatter(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesScatter = 1;
-// Emit phase (fallback when the entries overflowed): the three kernels
-// re-enumerate their units and write rows at trip_off.
-cudaError_t launch_emit_phase(const Job& j, int64_t n_events, const LaunchCfg& lc, bool persistent,
-                              cudaStream_t st);
-// One-launch form (no lists, queues or graphs): the static warp grid (1
-// launch), then the static block-per-event grid and the tail (1 + 4); its
-// emit fallback is the two static grids again (2).
-cudaError_t launch_plain_light(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-cudaError_t launch_plain_rest(const Job& j, const LaunchCfg& lc, cudaStream_t st);
-cudaError_t launch_plain_emit(const Job& j, const LaunchCfg& lc, cudaStream_t st);
 constexpr int kLaunchesPlainLight = 1, kLaunchesPlainRest = 5, kLaunchesPlainEmit = 2;
-// Per-hit z of events [ev0, ev1) from a per-layer table z_layer[S*3] (device
-// pointers; one launch).
-cudaError_t launch_expand_z(const int32_t* off, const float* z_layer, float* z, int64_t ev0, int64_t ev1, int S,
-                            int64_t n_hits, int n_sm, cudaStream_t st);
-size_t light_smem_bytes(int wpb);
-int light_max_blocks_per_sm(int wpb);
-int generic_max_blocks_per_sm(int threads);
-int heavy_max_blocks_per_sm();
-int medium_max_blocks_per_sm();
-size_t heavy_smem_bytes();
 constexpr int kHeavyTCap = 1 << 15;  // trigger triplets per event on the block-tile path
-const void* light_count_kernel_ptr();
+
 
 }  // namespace jpsi

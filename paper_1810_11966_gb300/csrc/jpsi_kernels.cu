@@ -48,8 +48,21 @@
 #include "jpsi_device.cuh"
 #include "jpsi_internal.h"
 
+// The file is compiled twice: JPSI_STREAM = 0 gives the event kernels
+// (namespace jpsi::basek), JPSI_STREAM = 1 the same kernels with the time
+// tests of free-streaming windows (jpsi::streamk); `if constexpr (kStream)`
+// keeps those tests, and their registers, out of the event build.
+#ifndef JPSI_STREAM
+#define JPSI_STREAM 0
+#endif
 namespace jpsi {
+#if JPSI_STREAM
+namespace streamk {
+#else
+namespace basek {
+#endif
 
+constexpr bool kStream = JPSI_STREAM != 0;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQCap = 128;                // pair queue entries per warp
 
@@ -118,7 +131,10 @@ struct WarpTile {
     uint16_t idx[Cfg::HCAP];
     uint32_t queue[kQCap];      // pair queue (enumeration)
     float2 T[kTCap];            // trigger triplet slopes
-    unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
+    union {
+        unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
+        float2 Tt[kTCap];                // or their (min t, max t) (free-streaming windows)
+    };
     uint8_t alive[kTCap];
     alignas(4) uint16_t bst[3 * Cfg::NC + 1];  // cell starts (cell counts while a layer is staged)
     LayerMeta meta[3];
@@ -236,6 +252,20 @@ __device__ __forceinline__ void prefetch_hits_l2(const Job& j, int32_t h0, int32
 }
 
 __device__ __forceinline__ int station_of(int si, int trig) { return si == 0 ? trig : (si - 1 < trig ? si - 1 : si); }
+
+// Free-streaming windows: are the times a, b, c coincident (max t <=
+// fl32(min t + dt))?  Also returns min and max.
+__device__ __forceinline__ bool coincident3(float a, float b, float c, float dt, float& tmin, float& tmax) {
+    tmin = fminf(fminf(a, b), c);
+    tmax = fmaxf(fmaxf(a, b), c);
+    return tmax <= __fadd_rn(tmin, dt);
+}
+
+// A partner triplet with times (pmin, pmax) of a trigger triplet with times
+// T = (min, max): itself coincident, and the six hits together.
+__device__ __forceinline__ bool partner_coincident(float pmin, float pmax, float2 T, float dt) {
+    return pmax <= __fadd_rn(pmin, dt) && fmaxf(pmax, T.y) <= __fadd_rn(fminf(pmin, T.x), dt);
+}
 
 // ------------------------------------------------------- event offsets
 
@@ -611,6 +641,7 @@ struct TSink {
     int n;      // warp-local counter when sh_n is null
     bool norec = false;  // a repeated enumeration: record no triplet entries
     unsigned long long* ijk = nullptr;  // distinct_hits: the triplets' packed hits beside T
+    float2* tt = nullptr;               // free-streaming windows: their (min t, max t) beside T
 };
 
 // Items of up to 32 lanes laid end to end: lane i owns items [excl, excl +
@@ -675,6 +706,7 @@ __device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int la
                                                int* sh_rank, int tag, int& count) {
     bool ok = false;
     float mx = 0.f, my = 0.f;
+    float2 tt = make_float2(0.f, 0.f);
     int ii = 0, jj = 0, kk = 0;
     if (has) {
         const int32_t base0 = t.meta[0].base, base1 = t.meta[1].base, base2 = t.meta[2].base;
@@ -685,6 +717,12 @@ __device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int la
         const float ys[3] = {__ldg(j.y + base0 + ii), __ldg(j.y + base1 + jj), __ldg(j.y + base2 + kk)};
         const float zs[3] = {__ldg(j.z + base0 + ii), __ldg(j.z + base1 + jj), __ldg(j.z + base2 + kk)};
         ok = fit_pass(xs, ys, zs, c, mx, my);
+        if constexpr (kStream) {  // coincident, and owned by this window
+            const int64_t e = unit / j.S;
+            ok = ok && coincident3(__ldg(j.t + base0 + ii), __ldg(j.t + base1 + jj), __ldg(j.t + base2 + kk), j.dt,
+                                   tt.x, tt.y) &&
+                 tt.x >= __ldg(j.wb + e) && tt.x < __ldg(j.wb + e + 1);
+        }
     }
     const unsigned mask = __ballot_sync(kFull, ok);
     if (mask) {
@@ -713,6 +751,7 @@ __device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int la
             if (ok && tb + rk < ts.cap) {
                 ts.T[tb + rk] = make_float2(mx, my);
                 if (ts.ijk) ts.ijk[tb + rk] = pack_ijk(ii, jj, kk);
+                if (ts.tt) ts.tt[tb + rk] = tt;
             }
         }
         if (!EMIT && j.tscr && !ts.norec) {  // record for the scatter pass
@@ -807,7 +846,7 @@ __device__ __forceinline__ void flush_pending(const Job& j, const TV& t, int lan
 }
 
 template <class TV>
-__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, int lane);
+__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, float2 Tt, int lane);
 
 // CHAIN-mode trigger slopes a block searches for while it enumerates a
 // station (block path): item n_rounds + i of the block-shared counter is
@@ -816,6 +855,7 @@ struct RoadItems {
     const float2* T;
     uint8_t* alive;
     int n;
+    const float2* Tt = nullptr;  // free-streaming windows: the slopes' (min t, max t)
 };
 
 // All passing triplets of the staged station (Sec. 3.2 steps 1-2) found by
@@ -850,7 +890,7 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
             const int ti = (i0 >> 5) - n_rounds;
             if (rd->alive[ti]) {
                 const float2 m = rd->T[ti];
-                const bool found = road_warp(j, t, c, m.x, m.y, lane);
+                const bool found = road_warp(j, t, c, m.x, m.y, rd->Tt ? rd->Tt[ti] : make_float2(0.f, 0.f), lane);
                 if (lane == 0 && !found) rd->alive[ti] = 0;
             }
             i0 = next_round();
@@ -888,7 +928,7 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
                 const int ti = (i0 >> 5) - n_rounds;
                 if (rd->alive[ti]) {
                     const float2 m = rd->T[ti];
-                    const bool found = road_warp(j, t, c, m.x, m.y, lane);
+                    const bool found = road_warp(j, t, c, m.x, m.y, rd->Tt ? rd->Tt[ti] : make_float2(0.f, 0.f), lane);
                     if (lane == 0 && !found) rd->alive[ti] = 0;
                 }
                 i0 = next_round();
@@ -940,7 +980,7 @@ struct WinIter {
 // trigger slopes (mx, my)?  Per-thread search through each layer's cells
 // inside the tube, row by row.
 template <class TV>
-__device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float my) {
+__device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float my, float2 Tt) {
     Win w[3];
     int a[3], e[3];  // first-row runs
 #pragma unroll
@@ -978,7 +1018,12 @@ __device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float m
                 const float ys[3] = {y0, y1, __ldg(j.y + h2)};
                 const float zs[3] = {z0, z1, __ldg(j.z + h2)};
                 float fx, fy;
-                if (fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c)) return true;
+                if (fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c)) {
+                    if constexpr (!kStream) return true;
+                    float pmin, pmax;
+                    coincident3(__ldg(j.t + h0), __ldg(j.t + h1), __ldg(j.t + h2), j.dt, pmin, pmax);
+                    if (partner_coincident(pmin, pmax, Tt, j.dt)) return true;
+                }
             }
         }
     }
@@ -993,8 +1038,8 @@ __device__ bool road(const Job& j, const TV& t, const Cuts& c, float mx, float m
 // with more than 32 kept hits hands the slope to road() on one lane (no such
 // limit).  Same answer as road(), warp-uniform.
 template <class TV>
-__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, int lane) {
-    float hx[3] = {0.f, 0.f, 0.f}, hy[3] = {0.f, 0.f, 0.f}, hz[3] = {0.f, 0.f, 0.f};
+__device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, float my, float2 Tt, int lane) {
+    float hx[3] = {0.f, 0.f, 0.f}, hy[3] = {0.f, 0.f, 0.f}, hz[3] = {0.f, 0.f, 0.f}, ht[3] = {0.f, 0.f, 0.f};
     int nk[3] = {0, 0, 0};
     bool over = false;
 #pragma unroll
@@ -1009,7 +1054,7 @@ __device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, fl
             for (int p0 = a; p0 < e; p0 += 32) {
                 const int p = p0 + lane;
                 bool keep = false;
-                float x = 0.f, y = 0.f, z = 0.f;
+                float x = 0.f, y = 0.f, z = 0.f, tm = 0.f;
                 if (p < e) {
                     const float2 P = t.P[p];
                     if (tube_ok(P.x, P.y, b, mx, my)) {
@@ -1017,6 +1062,7 @@ __device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, fl
                         x = __ldg(j.x + h);
                         y = __ldg(j.y + h);
                         z = __ldg(j.z + h);
+                        if constexpr (kStream) tm = __ldg(j.t + h);
                         keep = tube_pass(x, y, z, mx, my, c);
                     }
                 }
@@ -1029,11 +1075,12 @@ __device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, fl
                     const int src = __ffs(m) - 1;
                     m &= m - 1;
                     const float vx = __shfl_sync(kFull, x, src), vy = __shfl_sync(kFull, y, src),
-                                vz = __shfl_sync(kFull, z, src);
+                                vz = __shfl_sync(kFull, z, src), vt = __shfl_sync(kFull, tm, src);
                     if (lane == nk[l]) {
                         hx[l] = vx;
                         hy[l] = vy;
                         hz[l] = vz;
+                        ht[l] = vt;
                     }
                     ++nk[l];
                 }
@@ -1044,7 +1091,7 @@ __device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, fl
     }
     if (over) {
         bool f = false;
-        if (lane == 0) f = road(j, t, c, mx, my);
+        if (lane == 0) f = road(j, t, c, mx, my, Tt);
         return __shfl_sync(kFull, f, 0);
     }
     const int n01 = nk[0] * nk[1], total = n01 * nk[2];
@@ -1058,7 +1105,14 @@ __device__ bool road_warp(const Job& j, const TV& t, const Cuts& c, float mx, fl
         const float zs[3] = {__shfl_sync(kFull, hz[0], i0), __shfl_sync(kFull, hz[1], i1),
                              __shfl_sync(kFull, hz[2], i2)};
         float fx, fy;
-        if (__any_sync(kFull, fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c))) return true;
+        bool ok = fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c);
+        if constexpr (kStream) {
+            float pmin, pmax;
+            coincident3(__shfl_sync(kFull, ht[0], i0), __shfl_sync(kFull, ht[1], i1), __shfl_sync(kFull, ht[2], i2),
+                        j.dt, pmin, pmax);
+            ok = ok && partner_coincident(pmin, pmax, Tt, j.dt);
+        }
+        if (__any_sync(kFull, ok)) return true;
     }
     return false;
 }
@@ -1127,6 +1181,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
     const TV t{w.P, w.idx, w.bst, w.meta};
     TSink ts{false, w.T, kTCap, nullptr, 0};
     ts.ijk = j.distinct ? w.Tijk : nullptr;
+    ts.tt = kStream ? w.Tt : nullptr;
     int trig_count = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
@@ -1166,7 +1221,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
             for (int ti = lane; ti < ts.n; ti += 32)
                 if (w.alive[ti]) {
                     const float2 m = w.T[ti];
-                    if (!road(j, t, c, m.x, m.y)) w.alive[ti] = 0;
+                    if (!road(j, t, c, m.x, m.y, kStream ? w.Tt[ti] : make_float2(0.f, 0.f))) w.alive[ti] = 0;
                 }
             __syncwarp();
         }
@@ -1316,7 +1371,8 @@ __device__ __forceinline__ void prefetch_station_block(const Job& j, const Block
 // layers arrive while the first is staged.
 template <bool EMIT, class B>
 __device__ bool heavy_unit(const Job& j, BlockSmem<B>& sm, const Cuts& c, int gi, int64_t e, int s, TSink& ts,
-                           const float2* T, uint8_t* alive, int nT, int& cnt, int s_next = -1) {
+                           const float2* T, uint8_t* alive, int nT, int& cnt, int s_next = -1,
+                           const float2* Tt = nullptr) {
     using TV = TileView<B::NX, B::NY>;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t u = e * j.S + s;
@@ -1350,7 +1406,7 @@ __device__ bool heavy_unit(const Job& j, BlockSmem<B>& sm, const Cuts& c, int gi
     // the station's trigger-slope searches run on the warps beside its
     // enumeration rounds (both only read the staged tile)
     const bool empty = sm.meta[0].nlive == 0 || sm.meta[1].nlive == 0 || sm.meta[2].nlive == 0;
-    const RoadItems rd{T, alive, EMIT || empty ? 0 : nT};
+    const RoadItems rd{T, alive, EMIT || empty ? 0 : nT, Tt};
     enum_station<EMIT, true>(j, TV{sm.P, sm.idx, sm.bst, sm.meta}, sm.queue[wp], lane, c, ts, rows,
                        cnt_expected, u, &sm.s_rank, B::CLS, &sm.s_next, &rd);
     __syncthreads();
@@ -1395,14 +1451,17 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
     float2* T = j.tlist + (int64_t)blockIdx.x * j.tlist_cap;
     uint8_t* alive = j.talive + (int64_t)blockIdx.x * j.tlist_cap;
     unsigned long long* ijk = j.distinct ? j.tlist_ijk + (int64_t)blockIdx.x * j.tlist_cap : nullptr;
+    // free-streaming windows: the slopes' times in the same per-block storage
+    float2* tt = kStream ? reinterpret_cast<float2*>(j.tlist_ijk + (int64_t)blockIdx.x * j.tlist_cap) : nullptr;
     int trig_count = 0, nT = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
         TSink ts{(chain || j.distinct) && si == 0, T, j.tlist_cap, &sm.s_nT, 0};
         ts.ijk = ijk;
+        ts.tt = tt;
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
-        if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) return;
+        if (!heavy_unit<false>(j, sm, c, gi, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn, tt)) return;
         if (si > 0) {
             __syncthreads();
             continue;
@@ -1428,6 +1487,7 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
                 j.tpool[pb + i] = T[i];
                 j.tpool_alive[pb + i] = 1;
                 if (ijk) j.tpool_ijk[pb + i] = ijk[i];
+                if (tt) reinterpret_cast<float2*>(j.tpool_ijk)[pb + i] = tt[i];
             }
             if (tid == 0) j.hT[gi] = make_int2((int)pb, nT);
             return;
@@ -1467,7 +1527,10 @@ __device__ void heavy_event(const Job& j, HeavySmem& sm, const Cuts& c, int gi, 
 struct MediumSmem {
     BlockSmem<MedBCfg> b;
     float2 T[kTCap];
-    unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
+    union {
+        unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
+        float2 Tt[kTCap];                // or their (min t, max t) (free-streaming windows)
+    };
     uint8_t alive[kTCap];
 };
 
@@ -1498,9 +1561,12 @@ __device__ void medium_event(const Job& j, MediumSmem& ms, const Cuts& c, int64_
         __syncthreads();
         TSink ts{(chain || j.distinct) && si == 0, ms.T, kTCap, &sm.s_nT, 0};
         ts.ijk = j.distinct ? ms.Tijk : nullptr;
+        ts.tt = kStream ? ms.Tt : nullptr;
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
-        if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt, sn)) return;
+        if (!heavy_unit<false>(j, sm, c, kGiOwn, e, s, ts, ms.T, ms.alive, si == 0 ? 0 : nT, cnt, sn,
+                               kStream ? ms.Tt : nullptr))
+            return;
         __syncthreads();
         if (si > 0) continue;
         trig_count = cnt;
@@ -1665,7 +1731,8 @@ __global__ void __launch_bounds__(kHThreads, 3) k_heavy_units(const __grid_const
         load_event_offsets(j, sm, e);
         TSink ts{false, nullptr, 0, nullptr, 0};
         int cnt = 0;
-        heavy_unit<EMIT>(j, sm, c, gi, e, s, ts, j.tpool + hx, j.tpool_alive + hx, hy, cnt);
+        heavy_unit<EMIT>(j, sm, c, gi, e, s, ts, j.tpool + hx, j.tpool_alive + hx, hy, cnt, -1,
+                         kStream ? reinterpret_cast<const float2*>(j.tpool_ijk) + hx : nullptr);
         __syncthreads();
     }
 }
@@ -1709,7 +1776,7 @@ __device__ __forceinline__ GHit ghit(const Job& j, int64_t h) {
 }
 
 // Brute-force P2 search over every hit of every other station.
-__device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, float mx, float my) {
+__device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, float mx, float my, float2 Tt) {
     for (int s = 0; s < j.S; ++s) {
         if (s == j.trig) continue;
         const int32_t* o = soff + 3 * s;
@@ -1727,6 +1794,11 @@ __device__ bool road_global(const Job& j, const int32_t* soff, const Cuts& c, fl
                     if (!tube_pass(xs[2], ys[2], zs[2], mx, my, c)) continue;
                     float fx, fy;
                     found = fit_pass(xs, ys, zs, c, fx, fy) && chain_pass(xs, ys, zs, mx, my, c);
+                    if (kStream && found) {
+                        float pmin, pmax;
+                        coincident3(__ldg(j.t + h0), __ldg(j.t + h1), __ldg(j.t + h2), j.dt, pmin, pmax);
+                        found = partner_coincident(pmin, pmax, Tt, j.dt);
+                    }
                 }
             }
         }
@@ -1772,7 +1844,7 @@ __device__ void generic_candidates(const Job& j, const int32_t* soff, const Cuts
             const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
             float mx, my;
             if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
-            if (chain && !road_global(j, soff, c, mx, my)) continue;
+            if (chain && !road_global(j, soff, c, mx, my, make_float2(0.f, 0.f))) continue;  // (no streams here)
             const int r = atomicAdd(s_rank, 1);
             if (r < cap) out[r] = pack_ijk((int)i, (int)jx, (int)k);
         }
@@ -1843,6 +1915,12 @@ __device__ void generic_event(const Job& j, int64_t e, const GenShared& g) {
                 const float xs[3] = {hi.x, hj.x, hk.x}, ys[3] = {hi.y, hj.y, hk.y}, zs[3] = {hi.z, hj.z, hk.z};
                 float mx, my;
                 if (!fit_pass(xs, ys, zs, c, mx, my)) continue;
+                float2 Tt = make_float2(0.f, 0.f);
+                if constexpr (kStream) {  // coincident and owned by this window
+                    const bool co = coincident3(__ldg(j.t + o[0] + i), __ldg(j.t + o[1] + jx), __ldg(j.t + o[2] + k), j.dt,
+                                                Tt.x, Tt.y);
+                    if (!(co && Tt.x >= __ldg(j.wb + e) && Tt.x < __ldg(j.wb + e + 1))) continue;
+                }
                 ++local;
                 if (!EMIT && j.tscr) {
                     const int rk = atomicAdd(g.s_count, 1);
@@ -1869,7 +1947,7 @@ __device__ void generic_event(const Job& j, int64_t e, const GenShared& g) {
                         r[2] = (int32_t)k;
                     }
                 }
-                if (collect && road_global(j, soff, c, mx, my)) atomicAdd(g.s_cand, 1);
+                if (collect && road_global(j, soff, c, mx, my, Tt)) atomicAdd(g.s_cand, 1);
             }
         }
         if (!EMIT && !j.tscr && local) atomicAdd(g.s_count, local);
@@ -1985,6 +2063,7 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
     float2* T = ps.T;
     uint8_t* alive = ps.alive;
     unsigned long long* ijk = nullptr;  // distinct_hits: the candidates' packed hits (in the pool)
+    float2* tt = nullptr;               // free-streaming windows: the slopes' times (in the pool)
     int trig_count = 0, nT = 0;
     for (int si = 0; si < nproc; ++si) {
         const int s = station_of(si, j.trig);
@@ -1993,7 +2072,7 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         TSink ts{(chain || j.distinct) && si == 0, T, kPlainTCap, &sm.s_nT, 0};
         int cnt = 0;
         const int sn = si + 1 < nproc ? station_of(si + 1, j.trig) : -1;
-        if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn)) {
+        if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts, T, alive, si == 0 ? 0 : nT, cnt, sn, tt)) {
             __syncthreads();
             return j.ev_class[e] == kClsGeneric;
         }
@@ -2002,10 +2081,11 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
         trig_count = cnt;
         if (!chain && !j.distinct) break;
         nT = sm.s_nT;
-        if (nT > kPlainTCap || (j.distinct && nT >= 2)) {
+        if (nT > kPlainTCap || (j.distinct && nT >= 2) || (kStream && chain && nT > 0)) {
             // more slopes than the block keeps, or (distinct_hits) the
-            // candidates' hits wanted: room in the batch's pool, and the
-            // trigger station once more (same count, nothing recorded)
+            // candidates' hits or (free-streaming windows) the slopes' times
+            // wanted: room in the batch's pool, and the trigger station once
+            // more (same count, nothing recorded)
             if (tid == 0) sm.s_pool = atomicAdd(&j.ctrl->tpool_n, (unsigned long long)nT);
             __syncthreads();
             const unsigned long long pb = sm.s_pool;
@@ -2016,11 +2096,13 @@ __device__ bool plain_block_event(const Job& j, PlainSmem& ps, int64_t e) {
             T = j.tpool + pb;
             alive = j.tpool_alive + pb;
             if (j.distinct) ijk = j.tpool_ijk + pb;
+            if constexpr (kStream) tt = reinterpret_cast<float2*>(j.tpool_ijk) + pb;
             if (tid == 0) sm.s_nT = 0;
             __syncthreads();
             TSink ts2{true, T, nT, &sm.s_nT, 0};
             ts2.norec = true;
             ts2.ijk = ijk;
+            ts2.tt = tt;
             if (!heavy_unit<false>(j, sm, c, kGiPlain, e, s, ts2, nullptr, nullptr, 0, cnt)) {
                 __syncthreads();
                 return j.ev_class[e] == kClsGeneric;
@@ -2419,8 +2501,10 @@ cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg&
     return cudaGetLastError();
 }
 
+}  // namespace basek / streamk
 }  // namespace jpsi
 
+#if !JPSI_STREAM
 // ======================================================================
 // Allocation-free counting entry point (jpsi_select_noalloc, include/jpsi.h).
 //
@@ -2465,6 +2549,7 @@ static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
 extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batch* b, int32_t* track_counts,
                                            int32_t* unit_counts, void* cuda_stream) {
     using namespace jpsi;
+    using namespace jpsi::basek;
     if (!p || !b) return JPSI_EINVAL;
     if (p->n_stations < 1 || p->n_stations > kMaxStations || p->trigger_station < 0 ||
         p->trigger_station >= p->n_stations || (p->mode != JPSI_MODE_PAPER && p->mode != JPSI_MODE_CHAIN) ||
@@ -2532,4 +2617,4 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     if (ctl.n_medium + ctl.n_heavy + ctl.n_generic > 0) return JPSI_EINVAL;
     return JPSI_OK;
 }
-
+#endif  // !JPSI_STREAM

@@ -63,5 +63,5 @@ def test_struct_layouts_match_header(tmp_path):
 def test_built_for_sm103a():
     import paper_1810_11966_gb300.build as b
     b.build()
-    log = open(os.path.join(b.BUILD, "jpsi_kernels.cu.log")).read()
+    log = open(os.path.join(b.BUILD, "jpsi_kernels.log")).read()
     assert "compute_103a" in log and "sm_103a" in log
