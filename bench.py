@@ -199,6 +199,8 @@ def reference_arm(args, rank, world):
     import oracle
     import synth
     w = synth.WORKLOADS[args.workload]
+    if w.name == "poisson100_stream":
+        return reference_arm_stream(args, w, world)
     threads = os.cpu_count() or 1
     n = args.ref_events
     b = synth.generate(w, 0, n)
@@ -220,6 +222,28 @@ def reference_arm(args, rank, world):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"events [0, {n}) of {w.name} per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def reference_arm_stream(args, w, world):
+    """--impl reference on the free-streaming workload: the oracle's
+    free-streaming selection over the first --cpu-windows windows of a
+    2000-collision timeslice of the same recipe, per step."""
+    import synth
+    ts = synth.timeslice(w, 0, 2000)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = stream_cpu_baseline(ts, params_kw(args, w), n_windows=args.cpu_windows)
+        if i >= args.warmup:
+            vals.append(b["value"])
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "collisions/s on 1 GB300, free-streaming timeslice (bit-exact accept bits)",
+            "value": v, "unit": "collisions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "windows_per_step": args.cpu_windows, "mode": args.mode},
+            "cpu_baseline": {"value": v, "unit": "collisions/s", "cores": 1, "kind": "oracle",
+                             "sample": b["sample"]},
+            "e2e": {"value": v, "unit": "collisions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -303,6 +327,170 @@ def run_timeslices(args, w, dev, jp, torch):
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_free_stream(args, w, dev, jp, torch):
+    """A free-streaming timeslice (hits with times, no event association):
+    jpsi_run_stream builds one event per time window on the device and runs
+    the selection with the time tests; the metric is collisions per second.
+    Device-resident steps, then end to end from pinned host buffers (the
+    timeslice's copies in, the outputs' copies out, inside the timed
+    region)."""
+    import synth
+    t0 = time.perf_counter()
+    ts = synth.timeslice(w, 0, args.events or w.n_events)
+    gen_s = time.perf_counter() - t0
+    n_coll, n_hits, S = ts["n_collisions"], ts["n_hits"], w.n_stations
+    K = len(ts["bounds"]) - 1
+    host = {k: torch.from_numpy(np.ascontiguousarray(ts[k])).pin_memory()
+            for k in ("x", "y", "z", "t", "offsets", "bounds")}
+    d = {k: v.to(dev) for k, v in host.items()}
+    torch.cuda.synchronize()
+    p = jp.params(**params_kw(args, w))
+    ctx = jp.Context(p, device=dev.index, hbm_budget=64 << 30)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    tsd = jp.make_timeslice(d["x"], d["y"], d["z"], d["t"], d["offsets"], d["bounds"], ts["dt"])
+    nu = K * S
+    acc = torch.empty((K + 31) // 32, dtype=torch.int32, device=dev)
+    tc = torch.empty(K, dtype=torch.int32, device=dev)
+    toff = torch.empty(nu + 1, dtype=torch.int64, device=dev)
+    o = jp.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
+    ctx.check(jp.jpsi_run_stream(ctx.ctx, tsd, o, st))
+    cap = o.trip_needed
+    trip = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
+    o.triplets, o.trip_capacity = trip.data_ptr(), cap
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            ctx.check(fn(ctx.ctx, tsd, o, st))
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        jp.jpsi_timing_enable(ctx.ctx, True)
+        ev[0].record(stream)
+        for i in range(steps):
+            ctx.check(fn(ctx.ctx, tsd, o, st))
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        tm = jp.jpsi_timing_get(ctx.ctx)
+        jp.jpsi_timing_enable(ctx.ctx, False)
+        return ev[0].elapsed_time(ev[steps]), [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)], tm
+
+    clocks = Clocks(dev.index)
+    clocks.start()
+    tot_b, per_b, tm_b = timed(jp.jpsi_run_stream, args.steps, args.warmup)
+    clk = clocks.stop()
+    tot_p, per_p, _ = timed(jp.jpsi_run_stream_plain, max(args.steps // 2, 3), 3)
+    ref_tc = tc.cpu().numpy().copy()
+
+    # end to end: the timeslice from pinned host memory, the outputs back
+    hout = {"acc": torch.empty_like(acc, device="cpu").pin_memory(),
+            "tc": torch.empty_like(tc, device="cpu").pin_memory(),
+            "toff": torch.empty_like(toff, device="cpu").pin_memory(),
+            "trip": torch.empty_like(trip, device="cpu").pin_memory()}
+
+    def e2e_step():
+        for k in ("x", "y", "z", "t", "offsets", "bounds"):
+            d[k].copy_(host[k], non_blocking=True)
+        ctx.check(jp.jpsi_run_stream(ctx.ctx, tsd, o, st))
+        hout["acc"].copy_(acc, non_blocking=True)
+        hout["tc"].copy_(tc, non_blocking=True)
+        hout["toff"].copy_(toff, non_blocking=True)
+        hout["trip"][:cap].copy_(trip[:cap], non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(3):
+        e2e_step()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t1 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t1)
+    assert np.array_equal(hout["tc"].numpy(), ref_tc)
+    e2e_mean = sum(e2e_t) / len(e2e_t)
+    h2d = 16 * n_hits + 4 * (3 * S + 1) + 4 * (K + 1)
+    d2h = 4 * ((K + 31) // 32) + 4 * K + 8 * (nu + 1) + 12 * cap
+
+    ms_b = tot_b / args.steps
+    ms_p = tot_p / len(per_p)
+    runs = max(tm_b.runs, 1)
+    win_ms = tm_b.window_ms / runs
+    # the event-building phase moves at least: t and z of every hit (checks),
+    # x, y, z, t of every window-batch hit read and written once, the ranges
+    # (first hit, size, offset in 64 and 32 bits), and each triplet row read
+    # and written once by the mapping back
+    built = jp_window_hits(ts, p)
+    alg = 8 * n_hits + 32 * built + K * 3 * S * (4 + 4 + 8 + 4) + 24 * cap
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (win_ms / 1000.0) / 1e9
+    per_sorted = sorted(per_b)
+    line = {
+        "metric": "collisions/s on 1 GB300, free-streaming timeslice (bit-exact accept bits)",
+        "value": n_coll / (ms_b / 1000.0), "unit": "collisions/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "collisions": n_coll, "hits": n_hits, "windows": K,
+                   "window_ns": float(ts["bounds"][1] - ts["bounds"][0]), "dt_ns": ts["dt"],
+                   "rate_hz": w.extra["rate_hz"], "sigma_t_ns": w.extra["sigma_t_ns"], "mode": args.mode,
+                   "window_batch_hits": built, "form": "batched (persistent kernels + CUDA graph)",
+                   "l2": f"inputs ({16 * n_hits / 1e9:.1f} GB) larger than L2; no flush"},
+        "windows_per_s": K / (ms_b / 1000.0), "hits_per_s": n_hits / (ms_b / 1000.0),
+        "plain": {"value": n_coll / (ms_p / 1000.0), "ms_per_step": ms_p},
+        "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "max": per_sorted[-1]},
+        "phases_ms": {"event_building": win_ms, "light_count": tm_b.light_ms / runs,
+                      "count_rest": tm_b.count_rest_ms / runs, "emit": tm_b.emit_ms / runs},
+        "roofline": {"bound": "hbm", "kernel": "event building (k_win_check, k_win_ranges, scan, k_win_gather, "
+                     "k_win_rows)", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg},
+        "e2e": {"value": n_coll / e2e_mean, "unit": "collisions/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * e2e_mean,
+                "ms_samples": [round(1000 * v, 2) for v in e2e_t]},
+        "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "triplets_per_step": cap,
+        "accepted_windows": int(np.count_nonzero(ref_tc >= p.min_candidates)), "generate_s": gen_s,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = stream_cpu_baseline(ts, params_kw(args, w), n_windows=args.cpu_windows)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def jp_window_hits(ts, p):
+    """Hits of the window batch (the ranges the library gathers), counted on
+    the host from the timeslice: the trigger station's [b_k, fl32(b_k+1 + dt)],
+    the other stations (CHAIN) from just below b_k - dt to the same end."""
+    t, off, b = ts["t"], ts["offsets"], ts["bounds"].astype(np.float32)
+    dt = np.float32(ts["dt"])
+    end = (b[1:] + dt).astype(np.float32)
+    total = 0
+    for g in range(len(off) - 1):
+        s = g // 3
+        if p.mode == 0 and s != p.trigger_station:
+            continue
+        tg = t[off[g]:off[g + 1]]
+        b64 = b[:-1].astype(np.float64)
+        lod = (b64 - float(dt)) - (1e-6 * (np.abs(b64) + float(dt)) + 1e-30)
+        lo = b[:-1] if s == p.trigger_station else np.nextafter(lod.astype(np.float32), np.float32(-np.inf))
+        total += int((np.searchsorted(tg, end, side="right") - np.searchsorted(tg, lo, side="left")).clip(0).sum())
+    return total
+
+
+def stream_cpu_baseline(ts, kw, n_windows=12):
+    """The oracle's free-streaming selection, as it stands, on a bounded
+    sample: the first n_windows windows of the timeslice (one host thread),
+    scaled to collisions/s by the collisions whose time lies in them."""
+    import oracle
+    p = oracle.params(kw["n_stations"], kw["mode"], t_xz=kw["t_xz"], t_yz=kw["t_yz"])
+    b = ts["bounds"][: n_windows + 1]
+    t0 = time.perf_counter()
+    r = oracle.stream(p, ts, b, ts["dt"])
+    sec = time.perf_counter() - t0
+    assert r["status"] == 0
+    ct = ts["collision_times"]
+    n = int(np.count_nonzero((ct >= b[0]) & (ct < b[-1])))
+    return {"value": n / sec, "unit": "collisions/s", "cores": 1, "kind": "oracle",
+            "sample": f"windows 0..{n_windows - 1} ({n} collisions) of the timeslice, counts and rows, "
+                      f"{sec:.1f} s on one core"}
 
 
 def run_serving(args, w, dev, jp, torch):
@@ -530,6 +718,7 @@ def main():
     ap.add_argument("--slots", type=int, default=5)
     ap.add_argument("--requests", type=int, default=1000, help="requests per offered load (stream workload)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
+    ap.add_argument("--cpu-windows", type=int, default=12, help="windows of the stream workload's CPU sample")
     args = ap.parse_args()
     rank, world, local = dist_info()
     if args.warmup < 3 and not args.profile_steps:
@@ -557,6 +746,8 @@ def main():
         return run_serving(args, w, dev, jp, torch)
     if w.name == "poisson1500_6st":
         return run_stress(args, w, dev, jp, torch)
+    if w.name == "poisson100_stream":
+        return run_free_stream(args, w, dev, jp, torch)
     n_ev = args.events or w.n_events
     S = w.n_stations
 

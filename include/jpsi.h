@@ -169,6 +169,46 @@ jpsi_status jpsi_run(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, 
  * Errors as for jpsi_run. */
 jpsi_status jpsi_run_host(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, void *cuda_stream);
 
+/* Free-streaming selection: an extension.  The paper's Outlook (Sec. 8)
+ * notes that CBM's data acquisition will deliver free-streaming data, hits
+ * with times and no event association, so that hit times and event building
+ * have to enter the selection; it gives no rule.  This library's rule:
+ *   - a timeslice holds hits x, y, z, t (t in ns) grouped per (station,
+ *     layer): offsets [n_stations*3 + 1], hits of layer l of station s at
+ *     [offsets[s*3+l], offsets[s*3+l+1]), each group sorted by t
+ *     (non-decreasing, no NaN); z may be NULL with z_layer [n_stations*3];
+ *   - window k (0 .. n_windows-1) is [bounds[k], bounds[k+1]) (bounds
+ *     finite and strictly increasing);
+ *   - a triplet counts only when its hits are coincident, max t <=
+ *     fl32(min t + dt), and it belongs to the window holding its earliest
+ *     time, so a triplet across a boundary counts once;
+ *   - CHAIN: a passing trigger triplet T of window k is a candidate when
+ *     every other station holds a passing coincident triplet (anywhere in
+ *     the timeslice) compatible with T whose six hits together are
+ *     coincident.
+ * Outputs as for jpsi_run with windows in place of events; a triplet row
+ * (i, j, k) of unit w*S + s names hits offsets[3s] + i, offsets[3s+1] + j,
+ * offsets[3s+2] + k of the timeslice.  All pointers are device memory.  The
+ * library builds one event per window on the device (its hits within the
+ * window's time range) and keeps that copy in its scratch, so the budget
+ * must hold about 16 bytes per hit of the windows' ranges.  JPSI_EINVAL for a
+ * malformed timeslice (the time order, NaN times, z <= 0 and the bounds are
+ * checked on the device), for distinct_hits = 1, and when the windows'
+ * ranges hold 2^31 hits or more (split the timeslice).  jpsi_run_stream runs
+ * the batched form, jpsi_run_stream_plain the one-launch form; both give the
+ * same results. */
+typedef struct {
+    int64_t n_hits;
+    const float *x, *y, *z, *t;
+    const int32_t *offsets;   /* [n_stations * 3 + 1] */
+    const float *z_layer;     /* optional, as in jpsi_batch */
+    int64_t n_windows;
+    const float *bounds;      /* [n_windows + 1] */
+    float dt;                 /* coincidence width, ns: finite, >= 0 */
+} jpsi_timeslice;
+jpsi_status jpsi_run_stream(jpsi_ctx *ctx, const jpsi_timeslice *ts, jpsi_outputs *out, void *cuda_stream);
+jpsi_status jpsi_run_stream_plain(jpsi_ctx *ctx, const jpsi_timeslice *ts, jpsi_outputs *out, void *cuda_stream);
+
 /* How a context maps the work onto the GPU.  The paper has no counterpart
  * (its one kernel has one thread per event, Sec. 5.3); none of these knobs
  * changes a result.
@@ -236,14 +276,17 @@ jpsi_status jpsi_serve_stop(jpsi_ctx *ctx);
  * warp-per-event counting kernel (light_ms), the rest of the counting phase
  * (block-per-event kernel, accept bits, scan: count_rest_ms) and the
  * triplet-writing phase (emit_ms).  Enabling resets the totals.  The last
- * two fields report the batched form's current launch shape (warps per
+ * two int fields report the batched form's current launch shape (warps per
  * block and events per grab of the warp-per-event kernel, as chosen by
- * jpsi_autotune or the defaults 4 and 2). */
+ * jpsi_autotune or the defaults 4 and 2).  window_ms: free-streaming runs'
+ * event building (window ranges, their scan, the gather of the window
+ * batch, and the mapping of triplet rows back to the timeslice). */
 typedef struct {
     int64_t runs;
     int64_t kernel_launches; /* kernels of this library launched by those runs */
     double light_ms, count_rest_ms, emit_ms;
     int32_t light_wpb, light_grab;
+    double window_ms;
 } jpsi_timing;
 jpsi_status jpsi_timing_enable(jpsi_ctx *ctx, int enable);
 jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);

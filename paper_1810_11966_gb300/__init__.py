@@ -22,7 +22,7 @@ JPSI_MODE_PAPER, JPSI_MODE_CHAIN = 0, 1
 EXPORTS = ("jpsi_create", "jpsi_destroy", "jpsi_run_plain", "jpsi_run", "jpsi_run_host", "jpsi_autotune",
            "jpsi_serve_start", "jpsi_serve_submit", "jpsi_serve_wait", "jpsi_serve_stop", "jpsi_strerror",
            "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get", "jpsi_select_noalloc", "jpsi_get_tuning",
-           "jpsi_set_tuning")
+           "jpsi_set_tuning", "jpsi_run_stream", "jpsi_run_stream_plain")
 
 
 class JpsiError(RuntimeError):
@@ -48,10 +48,16 @@ class jpsi_outputs(ctypes.Structure):
                 ("triplets", ctypes.c_void_p), ("trip_capacity", ctypes.c_int64), ("trip_needed", ctypes.c_int64)]
 
 
+class jpsi_timeslice(ctypes.Structure):
+    _fields_ = [("n_hits", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("z_layer", ctypes.c_void_p),
+                ("n_windows", ctypes.c_int64), ("bounds", ctypes.c_void_p), ("dt", ctypes.c_float)]
+
+
 class jpsi_timing(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("light_ms", ctypes.c_double),
                 ("count_rest_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
-                ("light_wpb", ctypes.c_int32), ("light_grab", ctypes.c_int32)]
+                ("light_wpb", ctypes.c_int32), ("light_grab", ctypes.c_int32), ("window_ms", ctypes.c_double)]
 
 
 class jpsi_tuning(ctypes.Structure):
@@ -86,6 +92,10 @@ def load(build_if_missing: bool = False):
     for name in ("jpsi_run_plain", "jpsi_run", "jpsi_run_host"):
         f = getattr(lib, name)
         f.argtypes = [vp, P(jpsi_batch), P(jpsi_outputs), vp]
+        f.restype = st
+    for name in ("jpsi_run_stream", "jpsi_run_stream_plain"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, P(jpsi_timeslice), P(jpsi_outputs), vp]
         f.restype = st
     lib.jpsi_autotune.argtypes = [vp, P(jpsi_batch)]
     lib.jpsi_autotune.restype = st
@@ -154,6 +164,14 @@ def jpsi_run(ctx, batch: jpsi_batch, out: jpsi_outputs, stream=0) -> int:
 
 def jpsi_run_host(ctx, batch: jpsi_batch, out: jpsi_outputs, stream=0) -> int:
     return load().jpsi_run_host(ctx, ctypes.byref(batch), ctypes.byref(out), stream)
+
+
+def jpsi_run_stream(ctx, ts: jpsi_timeslice, out: jpsi_outputs, stream=0) -> int:
+    return load().jpsi_run_stream(ctx, ctypes.byref(ts), ctypes.byref(out), stream)
+
+
+def jpsi_run_stream_plain(ctx, ts: jpsi_timeslice, out: jpsi_outputs, stream=0) -> int:
+    return load().jpsi_run_stream_plain(ctx, ctypes.byref(ts), ctypes.byref(out), stream)
 
 
 def jpsi_autotune(ctx, sample: jpsi_batch) -> int:
@@ -247,6 +265,20 @@ def make_batch(x, y, z, offsets, n_events=None, n_hits=None, z_layer=None) -> jp
     return b
 
 
+def make_timeslice(x, y, z, t, offsets, bounds, dt, z_layer=None) -> jpsi_timeslice:
+    """A jpsi_timeslice over device tensors: hits grouped per (station, layer)
+    with offsets [3S+1], each group sorted by t; windows from bounds [K+1]."""
+    ts = jpsi_timeslice()
+    ts.n_hits = int(len(x))
+    ts.x, ts.y, ts.t, ts.offsets = _ptr(x), _ptr(y), _ptr(t), _ptr(offsets)
+    ts.z = None if z is None else _ptr(z)
+    ts.z_layer = None if z_layer is None else _ptr(z_layer)
+    ts.n_windows = max(int(len(bounds)) - 1, 0)
+    ts.bounds = _ptr(bounds)
+    ts.dt = float(dt)
+    return ts
+
+
 class Context:
     """Owns a jpsi context; ``select`` allocates outputs as torch tensors."""
 
@@ -274,6 +306,15 @@ class Context:
         if s != JPSI_OK:
             raise JpsiError(s, self.last_error())
 
+    def select_stream(self, x, y, z, t, offsets, bounds, dt, *, triplets=True, capacity=None, form="batched",
+                      stream=None, z_layer=None):
+        """Free-streaming selection of one timeslice (device tensors): windows
+        [bounds[k], bounds[k+1]) in place of events.  Returns what ``select``
+        returns; triplet rows index the timeslice's layer groups."""
+        ts = make_timeslice(x, y, z, t, offsets, bounds, dt, z_layer=z_layer)
+        run = {"batched": jpsi_run_stream, "plain": jpsi_run_stream_plain}[form]
+        return self._outputs(lambda o, st: run(self.ctx, ts, o, st), int(ts.n_windows), triplets, capacity, stream)
+
     def select(self, x, y, z, offsets, n_events, *, triplets=True, capacity=None, form="batched", stream=None,
                z_layer=None):
         """Runs the selection on device tensors.  Returns a dict with the run's
@@ -282,6 +323,11 @@ class Context:
         raised).  With capacity=None the call sizes the triplet buffer from a
         first counting run (two calls, like the library's own two-pass
         contract).  z may be None with a per-layer table z_layer (device)."""
+        b = make_batch(x, y, z, offsets, n_events, z_layer=z_layer)
+        run = {"batched": jpsi_run, "plain": jpsi_run_plain}[form]
+        return self._outputs(lambda o, st: run(self.ctx, b, o, st), n_events, triplets, capacity, stream)
+
+    def _outputs(self, call, n_events, triplets, capacity, stream):
         import torch
         dev = torch.device("cuda", self.device)
         S = self.p.n_stations
@@ -291,17 +337,15 @@ class Context:
             "track_counts": torch.empty(max(n_events, 1), dtype=torch.int32, device=dev),
             "trip_off": torch.empty(nu + 1, dtype=torch.int64, device=dev),
         }
-        b = make_batch(x, y, z, offsets, n_events, z_layer=z_layer)
         o = jpsi_outputs()
         o.accept_bits = out["accept_bits"].data_ptr()
         o.track_counts = out["track_counts"].data_ptr()
         o.trip_off = out["trip_off"].data_ptr()
-        run = {"batched": jpsi_run, "plain": jpsi_run_plain}[form]
         st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         tr = None
         if triplets:
             if capacity is None:
-                s = run(self.ctx, b, o, st)
+                s = call(o, st)
                 if s != JPSI_OK:
                     out.update(status=s, trip_needed=o.trip_needed, triplets=None, error=self.last_error())
                     return out
@@ -309,7 +353,7 @@ class Context:
             tr = torch.empty((max(capacity, 1), 3), dtype=torch.int32, device=dev)
             o.triplets = tr.data_ptr()
             o.trip_capacity = capacity
-        s = run(self.ctx, b, o, st)
+        s = call(o, st)
         out["status"] = s
         out["error"] = self.last_error() if s != JPSI_OK else ""
         out["trip_needed"] = o.trip_needed

@@ -68,7 +68,7 @@ struct RunState {
     Graph g_light, g_rest, g_emit, g_scatter;
     int g_cfg_id = -1;
     bool g_stream = false;  // the graphs hold the free-streaming kernels
-    cudaEvent_t ev[5] = {};  // timing marks: light start/end, rest end, emit start/end
+    cudaEvent_t ev[9] = {};  // timing marks: light start/end, rest end, emit start/end; window build and rows
     cudaEvent_t chunk_ev[kMaxChunks] = {};  // hit chunks copied (pipelined host run)
 };
 
@@ -134,6 +134,8 @@ struct jpsi_ctx {
     RunState rs;
     // device copies for jpsi_run_host
     DevBuf hx, hy, hz, hoff, hacc, htc, htoff, htrip;
+    // window batch of a free-streaming run: ranges, their scan, offsets, hits
+    DevBuf wlo, wcnt, woff, wbs, woff32, wx, wy, wz, wt;
     std::string last_error;
     std::mutex err_mu, cap_mu, alloc_mu;
     std::atomic<bool> timing{false};
@@ -256,7 +258,8 @@ jpsi_status check_batch(jpsi_ctx* c, const jpsi_batch* b, const jpsi_outputs* o,
 }
 
 // Prepares scratch and the job descriptor of a run.
-jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, bool host_hits) {
+jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs* o, bool host_hits,
+                    bool stream = false) {
     const int64_t S = c->p.n_stations;
     const int64_t ne = b->n_events, nu = ne * S;
     jpsi_status st;
@@ -272,11 +275,15 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     if ((st = ensure(c, rs.tpool, (size_t)tp * sizeof(float2), "trigger pool")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.tpool_alive, (size_t)tp, "trigger pool")) != JPSI_OK) return st;
     if ((st = ensure(c, rs.hT, (size_t)std::max<int64_t>(ne, 1) * sizeof(int2), "event list")) != JPSI_OK) return st;
-    if (c->p.distinct_hits &&
-        ((st = ensure(c, rs.dpair, (size_t)std::max<int64_t>(ne, 1), "disjoint flags")) != JPSI_OK ||
-         (st = ensure(c, rs.tlist_ijk, tl * sizeof(unsigned long long), "trigger lists")) != JPSI_OK ||
+    // distinct_hits: the candidates' packed hits; free-streaming windows: the
+    // trigger triplets' (earliest, latest) times, in the same arrays
+    if (c->p.distinct_hits && (st = ensure(c, rs.dpair, (size_t)std::max<int64_t>(ne, 1), "disjoint flags")) != JPSI_OK)
+        return st;
+    if ((c->p.distinct_hits || stream) &&
+        ((st = ensure(c, rs.tlist_ijk, tl * sizeof(unsigned long long), "trigger lists")) != JPSI_OK ||
          (st = ensure(c, rs.tpool_ijk, (size_t)tp * sizeof(unsigned long long), "trigger pool")) != JPSI_OK))
         return st;
+    static_assert(sizeof(float2) == sizeof(unsigned long long), "times share the packed-hit arrays");
     const int64_t ntiles = (nu + 4095) / 4096 + 1;
     if ((st = ensure(c, rs.block_sums, (size_t)ntiles * 8, "scan")) != JPSI_OK) return st;
     if (!o->track_counts && (st = ensure(c, rs.track_counts, (size_t)std::max<int64_t>(ne, 1) * 4, "track counts")))
@@ -319,7 +326,7 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.tpool = (float2*)rs.tpool.p;
     j.tpool_alive = (uint8_t*)rs.tpool_alive.p;
     j.tpool_cap = (int64_t)std::min(rs.tpool.bytes / sizeof(float2), rs.tpool_alive.bytes);
-    if (c->p.distinct_hits)
+    if (c->p.distinct_hits || stream)
         j.tpool_cap = std::min<int64_t>(j.tpool_cap, (int64_t)(rs.tpool_ijk.bytes / sizeof(unsigned long long)));
     j.hT = (int2*)rs.hT.p;
     j.accept_bits = o->accept_bits;
@@ -487,7 +494,7 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         bz.z = (const float*)rs.zfill.p;
         b = &bz;
     }
-    if ((s = prepare(c, rs, b, o, host_hits)) != JPSI_OK) return s;
+    if ((s = prepare(c, rs, b, o, host_hits, sj != nullptr)) != JPSI_OK) return s;
     if (sj) {  // free-streaming windows: the time tests' inputs
         rs.job.stream = 1;
         rs.job.dt = sj->dt;
@@ -813,6 +820,118 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
     return s;
 }
 
+// A free-streaming timeslice: windows become the events of a window batch
+// (ranges found and gathered on the device), the selection runs with the
+// time tests compiled in, and the triplet rows are moved back to timeslice
+// group indices.
+jpsi_status run_stream(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs* o, cudaStream_t st, bool batched) {
+    if (!ts || !o) return fail(c, JPSI_EINVAL, "null timeslice or outputs");
+    if (c->p.distinct_hits) return fail(c, JPSI_EINVAL, "distinct_hits is not defined for free-streaming windows");
+    const int64_t S = c->p.n_stations, S3 = 3 * S, K = ts->n_windows;
+    if (ts->n_hits < 0 || K < 0) return fail(c, JPSI_EINVAL, "negative sizes");
+    if (ts->n_hits >= ((int64_t)1 << 31)) return fail(c, JPSI_EINVAL, "n_hits must be < 2^31");
+    if (K > (((int64_t)1 << 31) - 2) / S3) return fail(c, JPSI_EINVAL, "too many windows for int32 offsets");
+    if (!(ts->dt >= 0.0f) || std::isinf(ts->dt)) return fail(c, JPSI_EINVAL, "dt must be finite and >= 0");
+    if (!ts->offsets || (K > 0 && !ts->bounds)) return fail(c, JPSI_EINVAL, "offsets or bounds missing");
+    if (ts->n_hits > 0 && (!ts->x || !ts->y || !ts->t || (!ts->z && !ts->z_layer)))
+        return fail(c, JPSI_EINVAL, "hit arrays missing");
+    if (o->triplets && !o->trip_off) return fail(c, JPSI_EINVAL, "triplets need trip_off");
+    if (o->trip_capacity < 0) return fail(c, JPSI_EINVAL, "negative triplet capacity");
+    const void* ptrs[] = {ts->x, ts->y, ts->z, ts->t, ts->offsets, ts->z_layer, ts->bounds, o->accept_bits,
+                          o->track_counts, o->trip_off, o->triplets};
+    for (const void* p : ptrs)
+        if (!device_accessible(c, p)) return fail(c, JPSI_EINVAL, "pointer is not device-accessible");
+    // the 3S+1 group offsets are checked here: the range search reads them
+    int32_t hoff[3 * kMaxStations + 1];
+    cudaError_t e = cudaMemcpyAsync(hoff, ts->offsets, (size_t)(S3 + 1) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "offsets readback");
+    if (hoff[0] != 0 || hoff[S3] != ts->n_hits) return fail(c, JPSI_EINVAL, "malformed offsets");
+    for (int g = 0; g < S3; ++g)
+        if (hoff[g + 1] < hoff[g]) return fail(c, JPSI_EINVAL, "malformed offsets");
+    const int64_t n = K * S3;
+    jpsi_status s;
+    if ((s = ensure(c, c->wlo, (size_t)std::max<int64_t>(n, 1) * 4, "window ranges")) ||
+        (s = ensure(c, c->wcnt, (size_t)std::max<int64_t>(n, 1) * 4, "window ranges")) ||
+        (s = ensure(c, c->woff, (size_t)(n + 1) * 8, "window ranges")) ||
+        (s = ensure(c, c->wbs, (size_t)((n + 4095) / 4096 + 1) * 8, "scan")) ||
+        (s = ensure(c, c->woff32, (size_t)(n + 1) * 4, "window offsets")))
+        return s;
+    RunState& rs = c->rs;
+    WinJob w{};
+    w.x = ts->x;
+    w.y = ts->y;
+    w.z = ts->z;
+    w.t = ts->t;
+    w.z_layer = ts->z_layer;
+    w.off = ts->offsets;
+    w.wb = ts->bounds;
+    w.n_hits = ts->n_hits;
+    w.K = K;
+    w.S = (int32_t)S;
+    w.trig = c->p.trigger_station;
+    w.chain = c->p.mode == JPSI_MODE_CHAIN && S > 1;
+    w.dt = ts->dt;
+    w.wlo = (int32_t*)c->wlo.p;
+    w.wcnt = (int32_t*)c->wcnt.p;
+    w.woff = (int64_t*)c->woff.p;
+    w.block_sums = (int64_t*)c->wbs.p;
+    w.off_out = (int32_t*)c->woff32.p;
+    w.ctrl = rs.d_ctrl;
+    w.n_sm = c->n_sm;
+    const bool timing = c->timing.load();
+    if ((e = cudaMemsetAsync(rs.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(c, e, "ctrl reset");
+    if (timing) cudaEventRecord(rs.ev[5], st);
+    if ((e = streamk::launch_window_ranges(w, st)) != cudaSuccess) return cuda_fail(c, e, "window ranges");
+    if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "ctrl readback");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "window ranges");
+    if (rs.h_ctrl->status & kStInvalid)
+        return fail(c, JPSI_EINVAL, "malformed timeslice: unsorted or NaN times, z <= 0, or bounds not increasing");
+    const int64_t total = rs.h_ctrl->trip_total;
+    if (total >= ((int64_t)1 << 31))
+        return fail(c, JPSI_EINVAL, "the windows' hit ranges hold 2^31 hits or more: split the timeslice");
+    const size_t hb = (size_t)std::max<int64_t>(total, 1) * 4;
+    if ((s = ensure(c, c->wx, hb, "window hits")) || (s = ensure(c, c->wy, hb, "window hits")) ||
+        (s = ensure(c, c->wz, hb, "window hits")) || (s = ensure(c, c->wt, hb, "window hits")))
+        return s;
+    w.xo = (float*)c->wx.p;
+    w.yo = (float*)c->wy.p;
+    w.zo = (float*)c->wz.p;
+    w.to = (float*)c->wt.p;
+    if ((e = streamk::launch_window_gather(w, st)) != cudaSuccess) return cuda_fail(c, e, "window gather");
+    if (timing) cudaEventRecord(rs.ev[6], st);
+    jpsi_batch wbat{};
+    wbat.n_events = K;
+    wbat.n_hits = total;
+    wbat.x = w.xo;
+    wbat.y = w.yo;
+    wbat.z = w.zo;
+    wbat.offsets = w.off_out;
+    const StreamJob sj{w.to, ts->bounds, ts->dt};
+    s = run_device(c, rs, &wbat, o, st, batched, false, kStreamL, &sj);
+    if (s != JPSI_OK) return s;
+    int launches = kLaunchesWindows;
+    const bool rows = o->triplets && o->trip_needed > 0;
+    if (rows) {
+        if (timing) cudaEventRecord(rs.ev[7], st);
+        if ((e = streamk::launch_window_rows(w, o->trip_off, o->triplets, st)) != cudaSuccess)
+            return cuda_fail(c, e, "window rows");
+        if (timing) cudaEventRecord(rs.ev[8], st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "window rows");
+        ++launches;
+    }
+    if (timing) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, rs.ev[5], rs.ev[6]);
+        if (rows) cudaEventElapsedTime(&b, rs.ev[7], rs.ev[8]);
+        std::lock_guard<std::mutex> lk(c->err_mu);
+        c->tm.kernel_launches += launches;
+        c->tm.window_ms += a + b;
+    }
+    return JPSI_OK;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -879,7 +998,8 @@ void jpsi_destroy(jpsi_ctx* c) {
     jpsi_serve_stop(c);
     cudaDeviceSynchronize();
     state_free(c, c->rs);
-    DevBuf* bufs[] = {&c->hx, &c->hy, &c->hz, &c->hoff, &c->hacc, &c->htc, &c->htoff, &c->htrip};
+    DevBuf* bufs[] = {&c->hx,  &c->hy,   &c->hz,  &c->hoff, &c->hacc, &c->htc, &c->htoff, &c->htrip, &c->wlo,
+                      &c->wcnt, &c->woff, &c->wbs, &c->woff32, &c->wx, &c->wy, &c->wz,   &c->wt};
     for (DevBuf* b : bufs) release(c, *b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
@@ -906,6 +1026,24 @@ jpsi_status jpsi_run(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* st
     jpsi_status s = check_batch(c, b, o, true);
     if (s != JPSI_OK) return s;
     return run_device(c, c->rs, b, o, (cudaStream_t)stream, true);
+}
+
+jpsi_status jpsi_run_stream(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs* o, void* stream) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    return run_stream(c, ts, o, (cudaStream_t)stream, true);
+}
+
+jpsi_status jpsi_run_stream_plain(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs* o, void* stream) {
+    if (!c) return JPSI_EINVAL;
+    BusyGuard g(c);
+    if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
+    cudaSetDevice(c->device);
+    c->last_error.clear();
+    return run_stream(c, ts, o, (cudaStream_t)stream, false);
 }
 
 jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {

@@ -168,6 +168,41 @@ JPSI_DECLARE_LAUNCHERS
 namespace streamk {
 JPSI_DECLARE_LAUNCHERS
 }
+
+// Event building for free-streaming timeslices: window k becomes event k
+// whose layer group g holds the timeslice hits of group g in a time range
+// (the trigger station: [b_k, fl32(b_k+1 + dt)]; the other stations of CHAIN
+// mode from a margin below b_k - dt to the same end; PAPER mode's other
+// stations: none).
+struct WinJob {
+    const float *x, *y, *z, *t;
+    const float* z_layer;  // per-group z when z is null
+    const int32_t* off;    // [3S + 1] timeslice layer groups (checked on the host)
+    const float* wb;       // [K + 1] window bounds
+    int64_t n_hits, K;
+    int32_t S, trig, chain;
+    float dt;
+    int32_t* wlo;          // [K*3S] first timeslice hit of each range
+    int32_t* wcnt;         // [K*3S] hits of each range
+    int64_t* woff;         // [K*3S + 1] exclusive scan of wcnt
+    int64_t* block_sums;   // scan scratch
+    int32_t* off_out;      // [K*3S + 1] the window batch's offsets
+    float *xo, *yo, *zo, *to;  // [total] the window batch's hits
+    Ctrl* ctrl;            // status (kStInvalid) and trip_total = the window batch's hits
+    int n_sm;
+};
+namespace streamk {
+//   launch_window_ranges: validates the timeslice (times sorted per group, no
+//     NaN; z > 0 where read; bounds finite and increasing), finds each
+//     window's ranges and scans their sizes (4 launches).
+//   launch_window_gather: the window batch's offsets and hits (1 launch).
+//   launch_window_rows: triplet rows from window-batch indices to timeslice
+//     layer-group indices (1 launch).
+cudaError_t launch_window_ranges(const WinJob& w, cudaStream_t st);
+cudaError_t launch_window_gather(const WinJob& w, cudaStream_t st);
+cudaError_t launch_window_rows(const WinJob& w, const int64_t* trip_off, int32_t* triplets, cudaStream_t st);
+}  // namespace streamk
+constexpr int kLaunchesWindows = 6;
 constexpr int kLaunchesLight = 1, kLaunchesRest = 10, kLaunchesEmit = 4;
 constexpr int kLaunchesScatter = 1;
 constexpr int kLaunchesPlainLight = 1, kLaunchesPlainRest = 5, kLaunchesPlainEmit = 2;

@@ -2501,6 +2501,181 @@ cudaError_t launch_emit_phase(const Job& job, int64_t n_events, const LaunchCfg&
     return cudaGetLastError();
 }
 
+#if JPSI_STREAM
+// ------------------------------------------- free-streaming event building
+//
+// A timeslice's hits are grouped by (station, layer), each group sorted by
+// time.  Window k = [b_k, b_k+1) becomes event k of a window batch: group g
+// of event k holds the group-g hits whose times lie in the window's range
+// (the trigger station: [b_k, fl32(b_k+1 + dt)], which holds every triplet
+// owned by the window; the other stations of CHAIN mode from a margin below
+// b_k - dt to the same end, which holds every partner that can be coincident
+// with such a triplet).  The selection kernels of this build then apply the
+// time tests themselves; the rows they write index the window batch and are
+// moved back to timeslice group indices at the end.
+
+// Last group q < S3 with so[q] <= h (so: the 3S+1 offsets, non-decreasing).
+__device__ __forceinline__ int group_of(const int32_t* so, int S3, int64_t h) {
+    int q = 0;
+#pragma unroll
+    for (int step = 32; step > 0; step >>= 1)
+        if (q + step < S3 && so[q + step] <= h) q += step;
+    return q;
+}
+
+// First index in [lo, hi) whose time is >= v (> v with STRICT); stays in
+// [lo, hi] whatever the times hold.
+template <bool STRICT>
+__device__ __forceinline__ int64_t t_search(const float* __restrict__ t, int64_t lo, int64_t hi, float v) {
+    while (lo < hi) {
+        const int64_t m = lo + ((hi - lo) >> 1);
+        const float tm = __ldg(t + m);
+        if (STRICT ? tm <= v : tm < v)
+            lo = m + 1;
+        else
+            hi = m;
+    }
+    return lo;
+}
+
+// The timeslice's own checks: times sorted within each group and not NaN,
+// z > 0 for every hit of a station the mode reads, window bounds finite and
+// strictly increasing.  Sets kStInvalid.
+__global__ void __launch_bounds__(256) k_win_check(const __grid_constant__ WinJob w) {
+    __shared__ int32_t so[3 * kMaxStations + 1];
+    const int S3 = 3 * w.S;
+    for (int i = threadIdx.x; i <= S3; i += blockDim.x) so[i] = w.off[i];
+    __syncthreads();
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t h = g0; h < w.n_hits; h += stride) {
+        const int g = group_of(so, S3, h);
+        const float th = __ldg(w.t + h);
+        if (isnan(th) || (h > so[g] && !(th >= __ldg(w.t + h - 1)))) bad = true;
+        if (w.z && (w.chain || g / 3 == w.trig) && __ldg(w.z + h) <= 0.f) bad = true;
+    }
+    for (int64_t k = g0; w.K > 0 && k <= w.K; k += stride) {  // no windows: bounds may be null
+        const float b = __ldg(w.wb + k);
+        if (!isfinite(b) || (k > 0 && !(b > __ldg(w.wb + k - 1)))) bad = true;
+    }
+    if (!w.z && blockIdx.x == 0 && threadIdx.x < S3) {
+        const int g = threadIdx.x;
+        if (so[g + 1] > so[g] && (w.chain || g / 3 == w.trig) && __ldg(w.z_layer + g) <= 0.f) bad = true;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&w.ctrl->status, kStInvalid);
+}
+
+// Each (window, group) range: first hit and size.
+__global__ void __launch_bounds__(256) k_win_ranges(const __grid_constant__ WinJob w) {
+    __shared__ int32_t so[3 * kMaxStations + 1];
+    const int S3 = 3 * w.S;
+    for (int i = threadIdx.x; i <= S3; i += blockDim.x) so[i] = w.off[i];
+    __syncthreads();
+    const int64_t n = w.K * S3, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const int64_t k = q / S3;
+        const int g = (int)(q - k * S3), s = g / 3;
+        int64_t lo = so[g], hi = so[g];
+        if (s == w.trig || w.chain) {
+            const float b0 = __ldg(w.wb + k), end = __fadd_rn(__ldg(w.wb + k + 1), w.dt);
+            float from = b0;
+            if (s != w.trig) {
+                // a partner's hits are no earlier than (latest trigger-triplet
+                // time) - dt, less one rounding of the sum: a margin of 1e-6
+                // relative covers it, the exact tests decide
+                double lod = (double)b0 - (double)w.dt;
+                lod -= 1e-6 * (fabs((double)b0) + (double)w.dt) + 1e-30;
+                from = nextafterf(__double2float_rn(lod), -INFINITY);
+            }
+            lo = t_search<false>(w.t, so[g], so[g + 1], from);
+            hi = t_search<true>(w.t, lo, so[g + 1], end);
+        }
+        w.wlo[q] = (int32_t)lo;
+        w.wcnt[q] = (int32_t)(hi - lo);
+    }
+}
+
+// The window batch: its offsets (from the scan) and its hits, one warp per
+// (window, group) range.
+__global__ void __launch_bounds__(256) k_win_gather(const __grid_constant__ WinJob w) {
+    const int S3 = 3 * w.S;
+    const int64_t n = w.K * S3;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += nwarps) {
+        const int64_t dst = w.woff[q];
+        const int64_t src = w.wlo[q];
+        const int cnt = w.wcnt[q];
+        if (lane == 0) w.off_out[q] = (int32_t)dst;
+        if (cnt == 0) continue;  // (a timeslice without hits may come without z and z_layer)
+        const float zl = w.z ? 0.f : __ldg(w.z_layer + (int)(q % S3));
+        for (int i = lane; i < cnt; i += 32) {
+            w.xo[dst + i] = __ldg(w.x + src + i);
+            w.yo[dst + i] = __ldg(w.y + src + i);
+            w.zo[dst + i] = w.z ? __ldg(w.z + src + i) : zl;
+            w.to[dst + i] = __ldg(w.t + src + i);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.off_out[n] = (int32_t)w.woff[n];
+}
+
+// Triplet rows of unit (k, s): window-batch layer indices plus the start of
+// the window's range in the timeslice group, less the group's start.
+__global__ void __launch_bounds__(256) k_win_rows(const __grid_constant__ WinJob w, const int64_t* trip_off,
+                                                  int32_t* tr) {
+    const int64_t nu = w.K * w.S;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nu; u += nwarps) {
+        const int64_t a = trip_off[u], b = trip_off[u + 1];
+        if (a == b) continue;
+        const int64_t k = u / w.S;
+        const int s = (int)(u - k * w.S);
+        const int64_t q = k * 3 * w.S + 3 * s;
+        const int32_t d0 = w.wlo[q] - __ldg(w.off + 3 * s), d1 = w.wlo[q + 1] - __ldg(w.off + 3 * s + 1),
+                      d2 = w.wlo[q + 2] - __ldg(w.off + 3 * s + 2);
+        for (int64_t r = a + lane; r < b; r += 32) {
+            tr[3 * r] += d0;
+            tr[3 * r + 1] += d1;
+            tr[3 * r + 2] += d2;
+        }
+    }
+}
+
+static unsigned win_grid(int64_t threads, int n_sm) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)n_sm * 8));
+}
+
+cudaError_t launch_window_ranges(const WinJob& w, cudaStream_t st) {
+    const int64_t n = w.K * 3 * w.S;
+    k_win_check<<<win_grid(std::max(w.n_hits, w.K + 1), w.n_sm), 256, 0, st>>>(w);
+    k_win_ranges<<<win_grid(n, w.n_sm), 256, 0, st>>>(w);
+    // the sizes' scan, with the scan kernels of the selection reading a job
+    // whose "units" are the (window, group) ranges
+    Job j{};
+    j.n_events = w.K;
+    j.S = 3 * w.S;
+    j.unit_counts = w.wcnt;
+    j.block_sums = w.block_sums;
+    j.trip_off = w.woff;
+    j.ctrl = w.ctrl;
+    k_scan_reduce<<<w.n_sm * 2, kScanThreads, 0, st>>>(j);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(j);
+    k_scan_down<<<w.n_sm * 2, kScanThreads, 0, st>>>(j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_gather(const WinJob& w, cudaStream_t st) {
+    k_win_gather<<<win_grid(w.K * 3 * w.S * 32, w.n_sm), 256, 0, st>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_rows(const WinJob& w, const int64_t* trip_off, int32_t* triplets, cudaStream_t st) {
+    k_win_rows<<<win_grid(w.K * w.S * 32, w.n_sm), 256, 0, st>>>(w, trip_off, triplets);
+    return cudaGetLastError();
+}
+#endif  // JPSI_STREAM
+
 }  // namespace basek / streamk
 }  // namespace jpsi
 

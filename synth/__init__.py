@@ -101,6 +101,15 @@ WORKLOADS = {
     "lognormal_stream": Workload("lognormal_stream", 4, 0, _Z4, radial="inv_r2", lognormal=True,
                                  p_two_mu=0.01, p_one_mu=0.05,
                                  extra={"slice_min": 2_000, "slice_max": 200_000, "rate_events_per_s": 1e7}),
+    # Free-streaming timeslice: collisions of the poisson100_1m recipe (own
+    # seed) at Poisson arrival times, 1e7 collisions/s (the interaction rate
+    # CBM aims at, Sec. 1-2), every hit at its collision's time plus
+    # N(0, 3 ns); windows of 100 ns, coincidence width 15 ns.  100 000
+    # collisions (10 ms of beam) per timeslice.
+    "poisson100_stream": Workload("poisson100_stream", 6, 100_000, _Z4, bg_lambda=100.0, radial="inv_r2",
+                                  p_two_mu=0.01, p_one_mu=0.05,
+                                  extra={"rate_hz": 1e7, "sigma_t_ns": 3.0, "window_ns": 100.0, "dt_ns": 15.0,
+                                         "t0_ns": 100.0}),
     # Combinatorial stress: 6 stations, Poisson(1500) background per layer,
     # 10 % of events with two muons, window 1.0 cm.
     "poisson1500_6st": Workload("poisson1500_6st", 5, 200_000, _Z6, bg_lambda=1500.0, radial="inv_r2",
@@ -235,6 +244,58 @@ def arrival_times(w: Workload | str, sizes):
     rng = np.random.Generator(np.random.PCG64(w.seed * 1_000_003 + 29))
     mean_gap = float(np.mean(sizes)) / w.extra["rate_events_per_s"]
     return np.cumsum(rng.exponential(mean_gap, size=len(sizes)))
+
+
+def timeslice(w: Workload | str, e0: int = 0, n_collisions: int | None = None, *, n_threads: int | None = None,
+              rate_hz: float | None = None, sigma_t_ns: float | None = None, window_ns: float | None = None,
+              dt_ns: float | None = None):
+    """A free-streaming timeslice made of collisions [e0, e0+n) of workload
+    ``w``'s event recipe.
+
+    Collision c arrives at t0 + the sum of c+1 exponential gaps (mean
+    1/rate); each of its hits is seen at that time plus N(0, sigma_t).  The
+    hits of all collisions are merged per (station, layer) and each group is
+    sorted by time (stably: ties keep collision, then hit order).  Times are
+    float32 ns from the timeslice start (so their resolution is that of a
+    float at the timeslice's length: 1 ns at 1e7 ns).  Windows are
+    [k W, (k+1) W) up to past the last hit.  Returns x, y, z, t (float32
+    [n_hits]), offsets (int32 [3S+1]), bounds (float32 [K+1]), dt,
+    n_stations, n_hits, collision_times (float64 ns), batch_offsets (the
+    generated events' offsets) and src (int64 [n_hits]: the index, in the
+    generated batch, of each timeslice hit)."""
+    if isinstance(w, str):
+        w = WORKLOADS[w]
+    ex = w.extra
+    n = w.n_events if n_collisions is None else n_collisions
+    rate = rate_hz if rate_hz is not None else ex.get("rate_hz", 1e7)
+    sig = sigma_t_ns if sigma_t_ns is not None else ex.get("sigma_t_ns", 3.0)
+    W = window_ns if window_ns is not None else ex.get("window_ns", 100.0)
+    dt = dt_ns if dt_ns is not None else ex.get("dt_ns", 15.0)
+    b = generate(w, e0, n, n_threads=n_threads)
+    S = w.n_stations
+    S3 = 3 * S
+    off = b["offsets"].astype(np.int64)
+    counts = np.diff(off)                                  # [n * S3]: hits per (collision, group)
+    rng = np.random.Generator(np.random.PCG64(w.seed * 1_000_003 + 41 + 7919 * e0))
+    tc = ex.get("t0_ns", 100.0) + np.cumsum(rng.exponential(1e9 / rate, size=n))
+    coll = np.repeat(np.repeat(np.arange(n), S3), counts)  # collision of each batch hit
+    grp = np.repeat(np.tile(np.arange(S3), n), counts)     # layer group of each batch hit
+    t_hit = (tc[coll] + rng.normal(0.0, sig, size=coll.size)).astype(np.float32)
+    by_group = np.argsort(grp, kind="stable")              # batch hits grouped, batch order kept
+    gsizes = np.bincount(grp, minlength=S3)
+    goff = np.zeros(S3 + 1, np.int64)
+    np.cumsum(gsizes, out=goff[1:])
+    src = np.empty(coll.size, np.int64)
+    for g in range(S3):
+        idx = by_group[goff[g]:goff[g + 1]]
+        src[goff[g]:goff[g + 1]] = idx[np.argsort(t_hit[idx], kind="stable")]
+    t = t_hit[src]
+    t_end = float(t.max()) if t.size else 0.0
+    K = int(np.floor(max(t_end, 0.0) / W)) + 1
+    bounds = (np.arange(K + 1, dtype=np.float64) * W).astype(np.float32)
+    return {"x": b["x"][src], "y": b["y"][src], "z": b["z"][src], "t": t, "offsets": goff.astype(np.int32),
+            "bounds": bounds, "dt": float(dt), "n_stations": S, "n_hits": int(src.size), "collision_times": tc,
+            "src": src, "batch_offsets": b["offsets"], "n_collisions": n, "workload": w.name}
 
 
 def checksum(batch) -> str:

@@ -41,3 +41,22 @@ def assert_same(gpu, ref, n_units, check_triplets=True, label=""):
         a = sorted_triplets(gpu["trip_off"], gpu["triplets"], n_units)
         b = sorted_triplets(ref["trip_off"], ref["triplets"], n_units)
         assert np.array_equal(a, b), label
+
+
+def gpu_select_stream(ctx, ts, bounds=None, dt=None, form="batched", triplets=True, capacity=None, z_layer=None):
+    """The free-streaming selection of a host timeslice (dict of numpy arrays)
+    through jpsi_run_stream / jpsi_run_stream_plain; outputs on the host."""
+    import torch
+    d = {k: torch.from_numpy(np.ascontiguousarray(ts[k])).cuda() for k in ("x", "y", "t", "offsets")}
+    z = None if z_layer is not None else torch.from_numpy(np.ascontiguousarray(ts["z"])).cuda()
+    zl = None if z_layer is None else torch.from_numpy(np.asarray(z_layer, np.float32)).cuda()
+    b = np.asarray(ts["bounds"] if bounds is None else bounds, np.float32)
+    db = torch.from_numpy(b.copy()).cuda()
+    r = ctx.select_stream(d["x"], d["y"], z, d["t"], d["offsets"], db, ts["dt"] if dt is None else dt,
+                          triplets=triplets, capacity=capacity, form=form, z_layer=zl)
+    torch.cuda.synchronize()
+    return {"status": r["status"], "trip_needed": r["trip_needed"], "error": r.get("error", ""),
+            "accept_bits": r["accept_bits"].cpu().numpy().view(np.uint32),
+            "track_counts": r["track_counts"].cpu().numpy(),
+            "trip_off": r["trip_off"].cpu().numpy(),
+            "triplets": None if r["triplets"] is None else r["triplets"].cpu().numpy()}

@@ -41,7 +41,7 @@ def test_struct_layouts_match_header(tmp_path):
     import subprocess
     import paper_1810_11966_gb300 as jp
     structs = {"jpsi_params": jp.jpsi_params, "jpsi_batch": jp.jpsi_batch, "jpsi_outputs": jp.jpsi_outputs,
-               "jpsi_timing": jp.jpsi_timing, "jpsi_tuning": jp.jpsi_tuning}
+               "jpsi_timing": jp.jpsi_timing, "jpsi_tuning": jp.jpsi_tuning, "jpsi_timeslice": jp.jpsi_timeslice}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "jpsi.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
