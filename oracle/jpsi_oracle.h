@@ -65,7 +65,7 @@ int jpsi_oracle_run(const jo_params *p, int64_t n_events, int64_t n_hits, const 
  * that holds its earliest time.  Passing triplets of window k at station s
  * are its coincident triplets that pass P1; in CHAIN mode a passing trigger
  * triplet T of window k is a candidate when every other station holds a
- * passing coincident triplet t (of any window) compatible with T (P2) whose
+ * passing coincident triplet t (anywhere in the timeslice) compatible with T (P2) whose
  * six hits together are coincident.  Window k is accepted when it holds at
  * least min_candidates candidates.  Outputs as for jpsi_oracle_run with
  * windows in place of events; triplet rows are indices into the timeslice's
