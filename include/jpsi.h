@@ -313,7 +313,7 @@ jpsi_status jpsi_timing_get(jpsi_ctx *ctx, jpsi_timing *out);
  *   unit_counts    int32 [n_events * n_stations] device, caller-owned: passing
  *                  triplets per unit (the counts jpsi_run scans into trip_off).
  * Only events that fit the warp tiles (192 hits per layer, 384 per station, at
- * most 64 passing trigger triplets in CHAIN mode, finite pruning bounds) are
+ * most 32 passing trigger triplets in CHAIN mode, finite pruning bounds) are
  * handled; a batch holding any other event returns JPSI_EINVAL (use jpsi_run).
  * distinct_hits = 1 is not supported here (JPSI_EINVAL): it changes accept
  * bits only, which this entry point does not return.

@@ -90,6 +90,7 @@ __device__ __forceinline__ bool tube_pass(float x, float y, float z, float mx, f
 
 struct HitPrep {
     float sx, sy, b;
+    float r, l1;  // r ~ 1/z and |s_x| + |s_y| (the parts of b the pair bound uses)
     bool live;  // all coordinates finite (else the hit can never pass)
     bool wild;  // live but s or b not finite: no pruning for its event
     bool zbad;  // z <= 0: invalid input
@@ -103,7 +104,9 @@ __device__ __forceinline__ HitPrep hit_prep(float x, float y, float z, float K) 
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(z));
     h.sx = __fmul_rn(x, iz);
     h.sy = __fmul_rn(y, iz);
-    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, __fadd_rn(fabsf(h.sx), fabsf(h.sy)))), kTau);
+    h.r = iz;
+    h.l1 = __fadd_rn(fabsf(h.sx), fabsf(h.sy));
+    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, h.l1)), kTau);
     // b finite implies s_x, s_y finite (b >= kappa |s|)
     h.wild = h.live & !((z >= 1.17549435e-38f) & (z < 8.50705917e+37f) & (h.b < INFINITY));
     return h;
@@ -115,6 +118,7 @@ __device__ __forceinline__ HitPrep hit_prep(float x, float y, float z, float K) 
 // s_x, s_y, hence finite x, y.
 struct HitFast {
     float sx, sy, b;
+    float r, l1;  // as in HitPrep
     bool ok;
 };
 
@@ -124,13 +128,41 @@ __device__ __forceinline__ HitFast hit_fast(float x, float y, float z, float K) 
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(z));
     h.sx = __fmul_rn(x, iz);
     h.sy = __fmul_rn(y, iz);
-    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, __fadd_rn(fabsf(h.sx), fabsf(h.sy)))), kTau);
+    h.r = iz;
+    h.l1 = __fadd_rn(fabsf(h.sx), fabsf(h.sy));
+    h.b = __fadd_rn(__fadd_rn(__fmul_rn(K, iz), __fmul_rn(kKappa, h.l1)), kTau);
     h.ok = (z >= 1.17549435e-38f) & (z < 8.50705917e+37f) & (h.b < INFINITY);
     return h;
 }
 
+// Pair bound of two layers, tighter than b_i + b_j.  For a triplet passing P1
+// the computed residuals of two of its hits satisfy r_i^2 + r_j^2 <= C (1 +
+// 4 eps) + 2^-148 (S <= C, and the partial sums of non-negative terms never
+// round below their parts), so with the per-hit relation above and
+// Cauchy-Schwarz
+//     |s_i - s_j| <= (1 + 2 eps)(|r_i|/z_i + |r_j|/z_j) + 2 eps |m|
+//                 <= (1 + 2 eps)(sqrt(C)(1 + 2 eps) + 2^-74) sqrt(1/z_i^2 + 1/z_j^2) + 2 eps |m|,
+// against sqrt(C)(1/z_i + 1/z_j) for b_i + b_j: a factor sqrt(2) at equal z.
+// With R_l the largest r ~ 1/z (1/z <= r (1 + 2^-21)) and S_l the largest
+// |s_x| + |s_y| of the stored hits of layer l,
+//     B_ab = K sqrt(R_a^2 + R_b^2) + kappa (S_a + S_b) + 2 tau
+// exceeds that for every pair of hits of layers a and b, by the argument for
+// b: K's relative slack 1e-4 covers the factors above and the rounding of
+// the squares, sum, root, product and sums here (a few 2^-24 each), its
+// 1e-20 covers 2^-74, and the kappa terms cover 2 eps |m| and the errors of
+// s.  When max(R_a, R_b) lies outside [2^-60, 2^60] (squares that could
+// overflow or lose the smaller term to underflow) R_a + R_b, which is never
+// below sqrt(R_a^2 + R_b^2), takes the root's place.
+__device__ __forceinline__ float pair_bound(float ra, float sa, float rb, float sb, float K) {
+    const float rm = fmaxf(ra, rb);
+    const float q = (rm >= 8.67361737988403547e-19f && rm <= 1.15292150460684698e+18f)
+                        ? __fsqrt_rn(__fadd_rn(__fmul_rn(ra, ra), __fmul_rn(rb, rb)))
+                        : __fadd_rn(ra, rb);
+    return __fadd_rn(__fadd_rn(__fmul_rn(K, q), __fmul_rn(kKappa, __fadd_rn(sa, sb))), 2.0f * kTau);
+}
+
 // May hits i and j belong to one passing triplet?  (never false for such a
-// pair when bb >= fl(b_i + b_j))
+// pair when bb >= fl(b_i + b_j), or bb >= the pair bound of their layers)
 __device__ __forceinline__ bool pair_ok(float sxi, float syi, float sxj, float syj, float bb) {
     return (fabsf(__fsub_rn(sxi, sxj)) <= bb) & (fabsf(__fsub_rn(syi, syj)) <= bb);
 }

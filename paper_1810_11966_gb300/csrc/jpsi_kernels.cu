@@ -5,7 +5,7 @@
 //   k_light    one warp per event.  Each station's hits are staged from HBM
 //              (coalesced loads into registers) into a per-warp shared tile
 //              sorted into cells (row = bin of s_y, column = bin of s_x; the
-//              small tile has one row of 64 columns).  Pairs (L0, L1) whose
+//              small tile has one row of 128 columns).  Pairs (L0, L1) whose
 //              slopes are close enough to belong to a passing triplet are
 //              found with the candidate windows of 32 L0 hits spread evenly
 //              over the lanes, compacted into a pair queue with ballot/popc,
@@ -14,17 +14,18 @@
 //              mode keeps the passing trigger triplets' slopes in the tile
 //              and searches the other stations' tiles for compatible
 //              triplets (P2).  Limits: 192 hits per layer, 384 per station,
-//              64 passing trigger triplets.
-//   k_medium   the same code on a larger warp tile (384 hits per layer, 960
-//              per station, 2 x 128 cells) for the events k_light passes on.
+//              32 passing trigger triplets.
+//   k_medium   the block-tile code on 2-warp blocks (384 hits per layer, 960
+//              per station, 16 x 32 cells) for the events k_light passes on.
 //   k_heavy, k_heavy_units, k_heavy_final
-//              8-warp blocks on a block tile (2048 hits per layer, 6144 per
-//              station, 4 x 128 cells), the warps taking L0 rounds from a
-//              shared counter.  k_sort_heavy orders these events largest
-//              first; k_heavy runs each one's trigger station and, in CHAIN
-//              mode, hands the other stations to k_heavy_units (one block
-//              per station, trigger slopes in a batch-wide pool) and
-//              k_heavy_final (alive slopes left per event).
+//              8-warp blocks on the block tile (2048 hits per layer, 5632 per
+//              station, 32 x 64 cells), the warps taking L0 rounds and
+//              trigger-slope searches from a shared counter.  k_sort_heavy
+//              orders these events largest first; k_heavy runs each one's
+//              trigger station and, in CHAIN mode, hands the other stations
+//              to k_heavy_units (one block per station, trigger slopes in a
+//              batch-wide pool) and k_heavy_final (alive slopes left per
+//              event).
 //   k_generic  one block per event, unpruned where the pruning bound is not
 //              finite (extreme coordinates) and no size limit: reads hits
 //              straight from global memory.
@@ -69,10 +70,11 @@ constexpr int kQCap = 128;                // pair queue entries per warp
 // warp path: tile shape per variant.  A layer's hits are sorted into
 // NY x NX cells: row = bin of s_y, column = bin of s_x (row-major), so the
 // cells of a slope window are one run of positions per row.  The small tile
-// uses one row (NY = 1): at about 100 hits per layer a second row saves
-// fewer candidate tests than its extra staging and window work costs.
+// uses one row (NY = 1): at about 100 hits per layer a second row, or a 16 x
+// 16 grid, saves fewer candidate tests than its extra staging, window work
+// and registers cost.
 constexpr int kTCap = 64;                 // passing trigger triplets per event (CHAIN)
-template <int RMAX_, int HCAP_, int NX_, int NY_, uint8_t CLS_, int WPB_>
+template <int RMAX_, int HCAP_, int NX_, int NY_, uint8_t CLS_, int WPB_, int TCAP_ = kTCap>
 struct WCfg {
     static constexpr int RMAX = RMAX_;              // hits per lane per layer
     static constexpr int LAYER_CAP = 32 * RMAX_;    // hits per layer
@@ -81,8 +83,12 @@ struct WCfg {
     static constexpr int NC = NX_ * NY_;            // cells per layer
     static constexpr uint8_t CLS = CLS_;            // event class of this path
     static constexpr int WPB = WPB_;                // warps per block (medium: fixed)
+    static constexpr int TCAP = TCAP_;              // passing trigger triplets kept (CHAIN)
 };
-using SmallCfg = WCfg<6, 384, 64, 1, kClsLight, 0>;      // 192 hits/layer, 384/station
+// the small tile: 192 hits per layer, 384 per station, one row of 128 cells
+// (a pair window of the 10^6-event workload holds 4.0 candidates instead of
+// 5.0 with 64 cells: 5 % less time), 32 passing trigger triplets kept
+using SmallCfg = WCfg<6, 384, 128, 1, kClsLight, 0, 32>;
 // the size limits of the medium tile (a 2-warp block tile, MedBCfg below)
 using MediumCfg = WCfg<12, 960, 32, 16, kClsMedium, 4>;  // 384 hits/layer, 960/station
 
@@ -109,6 +115,7 @@ constexpr int kHHCap = HeavyCfg::HCAP;
 struct LayerMeta {
     float lox, scx, loy, scy;  // cell map: column = bin of s_x, row = bin of s_y
     float bmax;                // largest pruning bound b of the layer
+    float rmax, smax;          // largest r ~ 1/z and |s_x| + |s_y| (pair bounds)
     int32_t base;              // global index of the layer's first hit
     int32_t pbase;             // tile position of the layer's first stored hit
     int32_t nlive;             // stored hits (finite coordinates)
@@ -129,15 +136,19 @@ template <class Cfg>
 struct WarpTile {
     float2 P[Cfg::HCAP];
     uint16_t idx[Cfg::HCAP];
-    uint32_t queue[kQCap];      // pair queue (enumeration)
-    float2 T[kTCap];            // trigger triplet slopes
     union {
-        unsigned long long Tijk[kTCap];  // their packed hits (distinct_hits)
-        float2 Tt[kTCap];                // or their (min t, max t) (free-streaming windows)
+        uint32_t queue[kQCap];  // pair queue (enumeration)
+        uint32_t cnt[Cfg::NC];  // cell counts of the layer being staged
     };
-    uint8_t alive[kTCap];
-    alignas(4) uint16_t bst[3 * Cfg::NC + 1];  // cell starts (cell counts while a layer is staged)
+    float2 T[Cfg::TCAP];        // trigger triplet slopes
+    union {
+        unsigned long long Tijk[Cfg::TCAP];  // their packed hits (distinct_hits)
+        float2 Tt[Cfg::TCAP];                // or their (min t, max t) (free-streaming windows)
+    };
+    uint8_t alive[Cfg::TCAP];
+    uint16_t bst[3 * Cfg::NC + 1];  // cell starts
     LayerMeta meta[3];
+    static_assert(Cfg::NC <= kQCap, "cell counts share the pair queue's memory");
 };
 
 template <class B>
@@ -150,7 +161,7 @@ struct BlockSmem {
     int32_t off[3 * kMaxStations + 1];
     int32_t wsum[B::WARPS];
     int red_i[B::WARPS][2];
-    float red_f[B::WARPS][5];
+    float red_f[B::WARPS][7];
     unsigned long long s_pool;
     long long s_item;
     int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy, s_next;
@@ -312,8 +323,9 @@ __device__ __forceinline__ int cell_count_add(uint16_t* cnt, int cell) {
 
 // Stages one layer into the warp tile.  Returns 0, or 1 (z <= 0), or 2 (a
 // hit whose pruning bound is not finite).  Hits are counted into cells with
-// shared-memory atomics (the order inside a cell is not fixed; results do
-// not depend on it) and written sorted by cell.
+// shared-memory atomics on 32-bit counters that share the pair queue's
+// memory (the queue is empty between stations; the order inside a cell is
+// not fixed, and results do not depend on it) and written sorted by cell.
 template <class Cfg>
 __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t base, int32_t n, int32_t pbase,
                                 int lane, int& nlive) {
@@ -321,12 +333,11 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     static_assert(NC % 32 == 0, "cells per layer");
     float sx[R], sy[R];
     int key[R];  // cell << 16 | rank in the cell once binned; -1: not stored
-    static_assert(CPL % 2 == 0, "two 16-bit cell counters per word");
-    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f, rmax = 0.0f, smax = 0.0f;
     bool bad = false;
     uint16_t* bst = w.bst + l * NC;  // the end of layer l is the start of layer l + 1
 #pragma unroll
-    for (int q = 0; q < CPL / 2; ++q) reinterpret_cast<uint32_t*>(bst)[CPL / 2 * lane + q] = 0;
+    for (int q = 0; q < CPL; ++q) w.cnt[CPL * lane + q] = 0u;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         key[r] = -1;
@@ -350,13 +361,15 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         loy = fminf(loy, p.sy);
         hiy = fmaxf(hiy, p.sy);
         bmax = fmaxf(bmax, p.b);
+        rmax = fmaxf(rmax, p.r);
+        smax = fmaxf(smax, p.l1);
     }
     if (__any_sync(kFull, bad)) {
         // some hit has an odd coordinate: classify every hit exactly
         bool zbad = false, wild = false;
         lox = loy = INFINITY;
         hix = hiy = -INFINITY;
-        bmax = 0.0f;
+        bmax = rmax = smax = 0.0f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (32 * r >= n) break;
@@ -373,6 +386,8 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
             loy = live ? fminf(loy, p.sy) : loy;
             hiy = live ? fmaxf(hiy, p.sy) : hiy;
             bmax = live ? fmaxf(bmax, p.b) : bmax;
+            rmax = live ? fmaxf(rmax, p.r) : rmax;
+            smax = live ? fmaxf(smax, p.l1) : smax;
         }
         if (__any_sync(kFull, zbad)) return 1;
         if (__any_sync(kFull, wild)) return 2;
@@ -383,8 +398,11 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         loy = warp_min(loy);
         hiy = warp_max(hiy);
     }
-    // the bounds are finite and > 0 here: their bit patterns order like the values
+    // the bounds and their parts are finite and >= 0 here: their bit patterns
+    // order like the values
     bmax = __int_as_float(__reduce_max_sync(kFull, __float_as_int(bmax)));
+    rmax = __int_as_float(__reduce_max_sync(kFull, __float_as_int(rmax)));
+    smax = __int_as_float(__reduce_max_sync(kFull, __float_as_int(smax)));
     const float scx = bin_scale(lox, hix, NX), scy = NY > 1 ? bin_scale(loy, hiy, NY) : 0.0f;
     __syncwarp();
 #pragma unroll
@@ -393,7 +411,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         if (key[r] >= 0) {
             const int row = NY > 1 ? slope_bin<NY>(sy[r], loy, scy) : 0;
             const int cell = row * NX + slope_bin<NX>(sx[r], lox, scx);
-            key[r] = (cell << 16) | cell_count_add(bst, cell);
+            key[r] = (cell << 16) | (int)atomicAdd(&w.cnt[cell], 1u);
         }
     }
     __syncwarp();
@@ -402,7 +420,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
-        cs[q] = (int)bst[CPL * lane + q];
+        cs[q] = (int)w.cnt[CPL * lane + q];
         cnt += cs[q];
     }
     const int incl = warp_incl_scan(cnt, lane);
@@ -431,6 +449,8 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         m.loy = loy;
         m.scy = scy;
         m.bmax = bmax;
+        m.rmax = rmax;
+        m.smax = smax;
         m.base = base;
         m.pbase = pbase;
         m.nlive = total;
@@ -466,7 +486,7 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
     float sx[B::RMAX], sy[B::RMAX];
     int key[B::RMAX];  // cell << 16 | rank in the cell once binned; -1: not stored
     static_assert(CPT % 2 == 0, "two 16-bit cell counters per word");
-    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f;
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f, rmax = 0.0f, smax = 0.0f;
     bool zbad = false, wild = false;
     uint16_t* bst = sm.bst + l * B::NC;  // the end of layer l is the start of layer l + 1
 #pragma unroll
@@ -494,12 +514,16 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         loy = live ? fminf(loy, p.sy) : loy;
         hiy = live ? fmaxf(hiy, p.sy) : hiy;
         bmax = live ? fmaxf(bmax, p.b) : bmax;
+        rmax = live ? fmaxf(rmax, p.r) : rmax;
+        smax = live ? fmaxf(smax, p.l1) : smax;
     }
     lox = warp_min(lox);
     hix = warp_max(hix);
     loy = warp_min(loy);
     hiy = warp_max(hiy);
     bmax = warp_max(bmax);
+    rmax = warp_max(rmax);
+    smax = warp_max(smax);
     const int fz = __any_sync(kFull, zbad), fw = __any_sync(kFull, wild);
     if (lane == 0) {
         sm.red_f[wp][0] = lox;
@@ -507,6 +531,8 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         sm.red_f[wp][2] = loy;
         sm.red_f[wp][3] = hiy;
         sm.red_f[wp][4] = bmax;
+        sm.red_f[wp][5] = rmax;
+        sm.red_f[wp][6] = smax;
         sm.red_i[wp][0] = fz;
         sm.red_i[wp][1] = fw;
     }
@@ -519,6 +545,8 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         loy = fminf(loy, sm.red_f[q][2]);
         hiy = fmaxf(hiy, sm.red_f[q][3]);
         bmax = fmaxf(bmax, sm.red_f[q][4]);
+        rmax = fmaxf(rmax, sm.red_f[q][5]);
+        smax = fmaxf(smax, sm.red_f[q][6]);
         anyz |= sm.red_i[q][0];
         anyw |= sm.red_i[q][1];
     }
@@ -577,6 +605,8 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         m.loy = loy;
         m.scy = scy;
         m.bmax = bmax;
+        m.rmax = rmax;
+        m.smax = smax;
         m.base = base;
         m.pbase = pbase;
         m.nlive = total;
@@ -630,6 +660,13 @@ __device__ __forceinline__ void win_runs(const TV& t, int l, const Win& w, int& 
 }
 
 // ---------------------------------------------------------- enumeration
+
+// Pair bound of the staged layers a and b (pair_bound in jpsi_device.cuh).
+template <class TV>
+__device__ __forceinline__ float layer_pair_bound(const TV& t, int a, int b, float K) {
+    const LayerMeta &ma = t.meta[a], &mb = t.meta[b];
+    return pair_bound(ma.rmax, ma.smax, mb.rmax, mb.smax, K);
+}
 
 // Where passing trigger triplets' slopes go (CHAIN mode, trigger station).
 // Warp path: a warp-local count; block path: a block-shared counter.
@@ -783,7 +820,7 @@ template <bool EMIT, bool COMPACT, class TV>
 __device__ void drain(const Job& j, const TV& t, const uint32_t* queue, int lane, const Cuts& c, int qn,
                       TSink& ts, int32_t* rows, int limit, int64_t unit, int* sh_rank, int tag, int& count,
                       Pending& pd) {
-    const float B02 = __fadd_rn(t.meta[0].bmax, t.meta[2].bmax), B12 = __fadd_rn(t.meta[1].bmax, t.meta[2].bmax);
+    const float B02 = layer_pair_bound(t, 0, 2, c.K), B12 = layer_pair_bound(t, 1, 2, c.K);
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int q = q0 + lane;
         uint32_t en = 0;
@@ -872,7 +909,7 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
     if (n0 == 0 || n1 == 0 || n2 == 0) return 0;
     const int n_rounds = (n0 + 31) >> 5;
     const int p0 = t.meta[0].pbase;
-    const float B01 = __fadd_rn(t.meta[0].bmax, t.meta[1].bmax);
+    const float B01 = layer_pair_bound(t, 0, 1, c.K);
     int qn = 0, count = 0;
     Pending pd;
     // rounds of 32 L0 hits: in order on the warp path; on the block path each
@@ -1179,7 +1216,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         if (!j.host_hits) prefetch_hits_l2(j, off_get(o, 3 * s0), off_get(o, 3 * s0 + 3), lane);
     }
     const TV t{w.P, w.idx, w.bst, w.meta};
-    TSink ts{false, w.T, kTCap, nullptr, 0};
+    TSink ts{false, w.T, Cfg::TCAP, nullptr, 0};
     ts.ijk = j.distinct ? w.Tijk : nullptr;
     ts.tt = kStream ? w.Tt : nullptr;
     int trig_count = 0;
@@ -1205,7 +1242,7 @@ __device__ void light_event_count(const Job& j, WarpTile<Cfg>& w, int lane, cons
         const int cnt = enum_station<false, false>(j, t, w.queue, lane, c, ts, nullptr, 0, e * S + s, nullptr, Cfg::CLS,
                                             nullptr);
         if (ts.on) {
-            if (ts.n > kTCap) {
+            if (ts.n > Cfg::TCAP) {
                 if (lane == 0) push_event(j, e, kClsHeavy);
                 return;
             }

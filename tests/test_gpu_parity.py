@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from gpu_helpers import assert_same, gpu_select
-from helpers import line_event, make_batch
+from helpers import layer_z, line_event, make_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -244,6 +244,59 @@ def test_dense_trigger_moves_to_block_tile(lib, oracle_mod):
         ctx = _ctx(lib, 2, mode)
         for form in ("plain", "batched"):
             assert_same(gpu_select(ctx, b, form=form), ref, 40, label=f"mode={mode} {form}")
+
+
+def _edge_residuals(z, C, pair, frac):
+    """Residuals of a triplet at the edge of the pair pruning bound: the fit's
+    residual vector r (orthogonal to z, so the least-squares slope is exactly
+    the one the hits were placed on) along e_a/z_a - e_b/z_b, the direction
+    that puts hits a and b furthest apart in slope for a given S = |r|^2 =
+    frac * C."""
+    z = np.asarray(z, float)
+    v = np.zeros(3)
+    v[pair[0]], v[pair[1]] = 1.0 / z[pair[0]], -1.0 / z[pair[1]]
+    r = v - (v @ z) / (z @ z) * z
+    return r * np.sqrt(frac * C / (r @ r))
+
+
+@pytest.mark.parametrize("t", [0.25, 9e-4, 4.0])
+def test_pair_bound_edge(lib, oracle_mod, t):
+    # Triplets whose two hits sit as far apart in slope as a passing fit
+    # allows (S just below, at and just above the cut), for every layer pair,
+    # in both planes, among 10, 250 and 700 background hits per layer (small,
+    # medium and block tiles): the pair pruning must keep every passing one.
+    rng = np.random.default_rng(41)
+    C = float(np.float32(2.0 * np.float32(t)))
+    zl = layer_z(2)
+    pairs = ((0, 1), (0, 2), (1, 2))
+    events = []
+    for n_bg in (10, 250, 700):
+        for _ in range(4):
+            ev = [[] for _ in range(6)]
+            for s in range(2):
+                z = zl[3 * s:3 * s + 3]
+                for px in pairs:
+                    for frac in (1.0 - 1e-3, 1.0 - 1e-6, 1.0, 1.0 + 1e-6):
+                        py = pairs[rng.integers(3)]
+                        mx, my = rng.uniform(-0.3, 0.3, 2)
+                        rx, ry = _edge_residuals(z, C, px, frac), _edge_residuals(z, C, py, frac)
+                        for li in range(3):
+                            ev[3 * s + li].append((mx * z[li] + rx[li], my * z[li] + ry[li], z[li]))
+                for li in range(3):
+                    rr = rng.uniform(15.0, 0.4 * z[li], n_bg)
+                    ph = rng.uniform(0, 2 * np.pi, n_bg)
+                    ev[3 * s + li] += [(float(a * np.cos(q)), float(a * np.sin(q)), z[li]) for a, q in zip(rr, ph)]
+                    rng.shuffle(ev[3 * s + li])
+            events.append(ev)
+    b = make_batch(events, 2)
+    for mode in (0, 1):
+        ref = _oracle(oracle_mod, 2, mode, t, t, b)
+        assert ref["status"] == 0
+        if mode == 1:  # the three triplets 1e-3 below the cut pass in every unit
+            assert (ref["unit_counts"] >= 3).all()
+        ctx = _ctx(lib, 2, mode, t, t)
+        for form in ("plain", "batched"):
+            assert_same(gpu_select(ctx, b, form=form), ref, len(events) * 2, label=f"t={t} mode={mode} {form}")
 
 
 def test_huge_layer_goes_unpruned(lib, oracle_mod):
