@@ -691,6 +691,26 @@ def run_stress(args, w, dev, jp, torch):
     ctx.close()
 
 
+def signal_diagnostic(w, e0, n, acc_words):
+    """Synthetic signal-finding rate, a diagnostic (the paper's efficiency
+    study needs its simulation samples): the fraction of events accepted
+    among those generated with two, one and no muons, over events [e0, e0+n)
+    of the workload, from the accept bits of the run."""
+    import synth
+    b = synth.generate(w, e0, n, truth=True)
+    counts = np.diff(b["offsets"].astype(np.int64)).reshape(n, -1).sum(axis=1)
+    ev = np.repeat(np.arange(n), counts)
+    n_mu = np.zeros(n, np.int64)
+    np.maximum.at(n_mu, ev, b["truth"].astype(np.int64))  # muons are numbered 1, 2 within an event
+    bits = (acc_words.view(np.uint32)[np.arange(n) // 32] >> (np.arange(n) % 32).astype(np.uint32)) & 1
+    out = {"events": n}
+    for k in (2, 1, 0):
+        sel = n_mu == k
+        out[f"events_{k}mu"] = int(sel.sum())
+        out[f"accepted_{k}mu"] = float(bits[sel].mean()) if sel.any() else None
+    return out
+
+
 def params_kw(args, w):
     t = w.window ** 2
     return {"n_stations": w.n_stations, "mode": 1 if args.mode == "chain" else 0, "t_xz": t, "t_yz": t}
@@ -909,6 +929,8 @@ def main():
         "triplets_per_step": cap,
         "generate_s": gen_s,
     }
+    if rank == 0:
+        line["signal_diagnostic"] = signal_diagnostic(w, e_first, min(100_000, n_ev), acc.cpu().numpy())
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), min(args.cpu_events, n_ev),
                                             n_single=min(10_000, n_ev))

@@ -270,6 +270,22 @@ jpsi_status jpsi_serve_wait(jpsi_ctx *ctx, uint64_t ticket, int timeout_ms, jpsi
                             double *latency_s);
 jpsi_status jpsi_serve_stop(jpsi_ctx *ctx);
 
+/* Host-side fault injection, for tests of the error paths (no counterpart in
+ * the paper).  Nothing is injected on the GPU: the library only behaves as if
+ * a host call had failed.
+ *   JPSI_FAULT_ALLOC  the context's next `count` device allocations fail as
+ *                     cudaMalloc would; the call that needed one returns
+ *                     JPSI_ENOMEM and the context stays usable.
+ *   JPSI_FAULT_RUN    the next `count` runs of serving slots fail with
+ *                     JPSI_ECUDA before anything is copied or launched.  A
+ *                     slot repeats a run that failed with anything but
+ *                     JPSI_EINVAL or JPSI_ECAPACITY once, and reports the
+ *                     second attempt's status: one injected failure is
+ *                     absorbed, two are reported.
+ * count = 0 clears the kind; count < 0 or an unknown kind: JPSI_EINVAL. */
+enum { JPSI_FAULT_ALLOC = 1, JPSI_FAULT_RUN = 2 };
+jpsi_status jpsi_inject_fault(jpsi_ctx *ctx, int kind, int count);
+
 /* Device-time accounting of runs, for roofline measurements (the paper times
  * its kernel and the transfers separately, Table 1).  While enabled,
  * each run records CUDA events on its stream around its phases: the

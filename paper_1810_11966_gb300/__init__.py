@@ -22,7 +22,8 @@ JPSI_MODE_PAPER, JPSI_MODE_CHAIN = 0, 1
 EXPORTS = ("jpsi_create", "jpsi_destroy", "jpsi_run_plain", "jpsi_run", "jpsi_run_host", "jpsi_autotune",
            "jpsi_serve_start", "jpsi_serve_submit", "jpsi_serve_wait", "jpsi_serve_stop", "jpsi_strerror",
            "jpsi_last_error", "jpsi_timing_enable", "jpsi_timing_get", "jpsi_select_noalloc", "jpsi_get_tuning",
-           "jpsi_set_tuning", "jpsi_run_stream", "jpsi_run_stream_plain")
+           "jpsi_set_tuning", "jpsi_run_stream", "jpsi_run_stream_plain", "jpsi_inject_fault")
+FAULT_ALLOC, FAULT_RUN = 1, 2
 
 
 class JpsiError(RuntimeError):
@@ -115,6 +116,8 @@ def load(build_if_missing: bool = False):
     lib.jpsi_timing_enable.restype = st
     lib.jpsi_timing_get.argtypes = [vp, P(jpsi_timing)]
     lib.jpsi_timing_get.restype = st
+    lib.jpsi_inject_fault.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.jpsi_inject_fault.restype = st
     lib.jpsi_select_noalloc.argtypes = [P(jpsi_params), P(jpsi_batch), vp, vp, vp]
     lib.jpsi_select_noalloc.restype = st
     lib.jpsi_get_tuning.argtypes = [vp, P(jpsi_tuning)]
@@ -208,6 +211,11 @@ def jpsi_timing_get(ctx) -> jpsi_timing:
     if s != JPSI_OK:
         raise JpsiError(s, "jpsi_timing_get")
     return t
+
+
+def jpsi_inject_fault(ctx, kind: int, count: int) -> int:
+    """Host-side fault injection for tests (FAULT_ALLOC or FAULT_RUN)."""
+    return load().jpsi_inject_fault(ctx, kind, count)
 
 
 def jpsi_get_tuning(ctx) -> jpsi_tuning:

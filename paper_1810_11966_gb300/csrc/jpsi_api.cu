@@ -2,6 +2,7 @@
 // plain and batched run forms, host-buffer runs, the autotuner and the
 // continuous-batching serving loop.  All device work is in jpsi_kernels.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -25,6 +26,15 @@ using namespace jpsi;
 using namespace jpsi::basek;  // the event kernels; stream runs take jpsi::streamk's launchers
 
 namespace {
+
+// NVTX range around a host call (header-only NVTX: a no-op unless a profiler
+// such as Nsight Systems is attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 constexpr size_t kDefaultBudget = (size_t)8 << 30;
 constexpr int kMaxChunks = 8;            // jpsi_run_host pipelines copies and counting in up to 8 chunks
@@ -151,6 +161,8 @@ struct jpsi_ctx {
     uint64_t next_ticket = 1;
     bool serving = false, stopping = false;
     std::vector<std::condition_variable*> slot_cv;
+    // host-side fault injection (jpsi_inject_fault)
+    std::atomic<int> fault_alloc{0}, fault_run{0};
 };
 
 namespace {
@@ -179,6 +191,14 @@ jpsi_status cuda_fail(jpsi_ctx* c, cudaError_t e, const char* where) {
     return fail(c, JPSI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Takes one injected fault of a kind, if any is left.
+bool take_fault(std::atomic<int>& left) {
+    int v = left.load();
+    while (v > 0)
+        if (left.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
 // Grows a device buffer within the context budget (contents not kept).
 jpsi_status ensure(jpsi_ctx* c, DevBuf& b, size_t bytes, const char* what) {
     if (bytes <= b.bytes) return JPSI_OK;
@@ -187,6 +207,7 @@ jpsi_status ensure(jpsi_ctx* c, DevBuf& b, size_t bytes, const char* what) {
     const size_t extra = nb - b.bytes;
     if (c->used + extra > c->budget)
         return fail(c, JPSI_ENOMEM, std::string("scratch for ") + what + " exceeds the device budget");
+    if (take_fault(c->fault_alloc)) return fail(c, JPSI_ENOMEM, std::string("injected allocation failure for ") + what);
     void* p = nullptr;
     if (cudaMalloc(&p, nb) != cudaSuccess) {
         cudaGetLastError();
@@ -1008,6 +1029,7 @@ void jpsi_destroy(jpsi_ctx* c) {
 
 jpsi_status jpsi_run_plain(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_run_plain");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     cudaSetDevice(c->device);
@@ -1019,6 +1041,7 @@ jpsi_status jpsi_run_plain(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, vo
 
 jpsi_status jpsi_run(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_run");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     cudaSetDevice(c->device);
@@ -1030,6 +1053,7 @@ jpsi_status jpsi_run(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* st
 
 jpsi_status jpsi_run_stream(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs* o, void* stream) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_run_stream");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     cudaSetDevice(c->device);
@@ -1039,6 +1063,7 @@ jpsi_status jpsi_run_stream(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs*
 
 jpsi_status jpsi_run_stream_plain(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_outputs* o, void* stream) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_run_stream_plain");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     cudaSetDevice(c->device);
@@ -1048,6 +1073,7 @@ jpsi_status jpsi_run_stream_plain(jpsi_ctx* c, const jpsi_timeslice* ts, jpsi_ou
 
 jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, void* stream) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_run_host");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     cudaSetDevice(c->device);
@@ -1068,6 +1094,17 @@ jpsi_status jpsi_run_host(jpsi_ctx* c, const jpsi_batch* b, jpsi_outputs* o, voi
     if (s != JPSI_EBUSY) return s;
     return run_host_with(c, c->rs, b, o, c->hx, c->hy, c->hz, c->hoff, c->hacc, c->htc, c->htoff, c->htrip, -1,
                          (cudaStream_t)stream);
+}
+
+jpsi_status jpsi_inject_fault(jpsi_ctx* c, int kind, int count) {
+    if (!c || count < 0) return JPSI_EINVAL;
+    if (kind == JPSI_FAULT_ALLOC)
+        c->fault_alloc.store(count);
+    else if (kind == JPSI_FAULT_RUN)
+        c->fault_run.store(count);
+    else
+        return JPSI_EINVAL;
+    return JPSI_OK;
 }
 
 jpsi_status jpsi_timing_enable(jpsi_ctx* c, int enable) {
@@ -1111,6 +1148,7 @@ jpsi_status jpsi_set_tuning(jpsi_ctx* c, const jpsi_tuning* t) {
 
 jpsi_status jpsi_autotune(jpsi_ctx* c, const jpsi_batch* sample) {
     if (!c) return JPSI_EINVAL;
+    Range r("jpsi_autotune");
     BusyGuard g(c);
     if (!g.ok) return fail(c, JPSI_EBUSY, "context in use");
     if (c->serving) return fail(c, JPSI_EBUSY, "tuning is fixed while serving");
@@ -1209,8 +1247,16 @@ static void slot_worker(jpsi_ctx* c, int si) {
         jpsi_batch b = sl->batch;
         jpsi_outputs* o = sl->out;
         lk.unlock();
-        jpsi_status s = run_host_with(c, sl->rs, &b, o, sl->x, sl->y, sl->z, sl->off, sl->accept, sl->tracks,
-                                      sl->trip_off, sl->triplets, sl->cap_trip, sl->stream);
+        Range r("jpsi_serve slot run");
+        auto run_once = [&]() -> jpsi_status {
+            if (take_fault(c->fault_run)) return fail(c, JPSI_ECUDA, "injected run failure");
+            return run_host_with(c, sl->rs, &b, o, sl->x, sl->y, sl->z, sl->off, sl->accept, sl->tracks,
+                                 sl->trip_off, sl->triplets, sl->cap_trip, sl->stream);
+        };
+        jpsi_status s = run_once();
+        // one more attempt after a failure that is not the request's own
+        // fault (an invalid batch or too small an output buffer fails again)
+        if (s != JPSI_OK && s != JPSI_EINVAL && s != JPSI_ECAPACITY) s = run_once();
         const double lat =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - sl->t_submit).count();
         lk.lock();
