@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -136,7 +137,7 @@ template <class Cfg>
 struct WarpTile {
     float2 P[Cfg::HCAP];
     uint16_t idx[Cfg::HCAP];
-    union {
+    union alignas(16) {
         uint32_t queue[kQCap];  // pair queue (enumeration)
         uint32_t cnt[Cfg::NC];  // cell counts of the layer being staged
     };
@@ -146,7 +147,7 @@ struct WarpTile {
         float2 Tt[Cfg::TCAP];                // or their (min t, max t) (free-streaming windows)
     };
     uint8_t alive[Cfg::TCAP];
-    uint16_t bst[3 * Cfg::NC + 1];  // cell starts
+    alignas(8) uint16_t bst[3 * Cfg::NC + 1];  // cell starts
     LayerMeta meta[3];
     static_assert(Cfg::NC <= kQCap, "cell counts share the pair queue's memory");
 };
@@ -161,7 +162,7 @@ struct BlockSmem {
     int32_t off[3 * kMaxStations + 1];
     int32_t wsum[B::WARPS];
     int red_i[B::WARPS][2];
-    float red_f[B::WARPS][7];
+    int red_k[B::WARPS][7];
     unsigned long long s_pool;
     long long s_item;
     int s_gi, s_rank, s_nT, s_cand, s_hx, s_hy, s_next;
@@ -330,14 +331,14 @@ template <class Cfg>
 __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t base, int32_t n, int32_t pbase,
                                 int lane, int& nlive) {
     constexpr int R = Cfg::RMAX, NX = Cfg::NX, NY = Cfg::NY, NC = Cfg::NC, CPL = NC / 32;  // cells per lane
-    static_assert(NC % 32 == 0, "cells per layer");
+    static_assert(NC % 128 == 0, "cells per layer: four 32-bit counters (16 bytes) per lane");
     float sx[R], sy[R];
     int key[R];  // cell << 16 | rank in the cell once binned; -1: not stored
     float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY, bmax = 0.0f, rmax = 0.0f, smax = 0.0f;
     bool bad = false;
     uint16_t* bst = w.bst + l * NC;  // the end of layer l is the start of layer l + 1
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) w.cnt[CPL * lane + q] = 0u;
+    for (int q = 0; q < CPL / 4; ++q) reinterpret_cast<uint4*>(w.cnt)[CPL / 4 * lane + q] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         key[r] = -1;
@@ -358,8 +359,10 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         sy[r] = p.sy;
         lox = fminf(lox, p.sx);
         hix = fmaxf(hix, p.sx);
-        loy = fminf(loy, p.sy);
-        hiy = fmaxf(hiy, p.sy);
+        if constexpr (NY > 1) {
+            loy = fminf(loy, p.sy);
+            hiy = fmaxf(hiy, p.sy);
+        }
         bmax = fmaxf(bmax, p.b);
         rmax = fmaxf(rmax, p.r);
         smax = fmaxf(smax, p.l1);
@@ -383,8 +386,10 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
             key[r] = live ? 0 : -1;
             lox = live ? fminf(lox, p.sx) : lox;
             hix = live ? fmaxf(hix, p.sx) : hix;
-            loy = live ? fminf(loy, p.sy) : loy;
-            hiy = live ? fmaxf(hiy, p.sy) : hiy;
+            if constexpr (NY > 1) {
+                loy = live ? fminf(loy, p.sy) : loy;
+                hiy = live ? fmaxf(hiy, p.sy) : hiy;
+            }
             bmax = live ? fmaxf(bmax, p.b) : bmax;
             rmax = live ? fmaxf(rmax, p.r) : rmax;
             smax = live ? fmaxf(smax, p.l1) : smax;
@@ -419,17 +424,23 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
     int cs[CPL];
     int cnt = 0;
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-        cs[q] = (int)w.cnt[CPL * lane + q];
-        cnt += cs[q];
+    for (int q = 0; q < CPL / 4; ++q) {
+        const uint4 c4 = reinterpret_cast<const uint4*>(w.cnt)[CPL / 4 * lane + q];
+        cs[4 * q] = (int)c4.x;
+        cs[4 * q + 1] = (int)c4.y;
+        cs[4 * q + 2] = (int)c4.z;
+        cs[4 * q + 3] = (int)c4.w;
     }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) cnt += cs[q];
     const int incl = warp_incl_scan(cnt, lane);
     const int total = __shfl_sync(kFull, incl, 31);
     int run = pbase + incl - cnt;
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-        bst[CPL * lane + q] = (uint16_t)run;
-        run += cs[q];
+    for (int q = 0; q < CPL / 4; ++q) {  // four 16-bit starts per 8-byte store
+        const uint32_t s0 = (uint32_t)run, s1 = s0 + cs[4 * q], s2 = s1 + cs[4 * q + 1], s3 = s2 + cs[4 * q + 2];
+        reinterpret_cast<uint2*>(bst)[CPL / 4 * lane + q] = make_uint2((s0 & 0xffffu) | (s1 << 16), (s2 & 0xffffu) | (s3 << 16));
+        run = (int)s3 + cs[4 * q + 3];
     }
     if (lane == 31) bst[NC] = (uint16_t)(pbase + total);
     __syncwarp();
@@ -517,40 +528,34 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         rmax = live ? fmaxf(rmax, p.r) : rmax;
         smax = live ? fmaxf(smax, p.l1) : smax;
     }
-    lox = warp_min(lox);
-    hix = warp_max(hix);
-    loy = warp_min(loy);
-    hiy = warp_max(hiy);
-    bmax = warp_max(bmax);
-    rmax = warp_max(rmax);
-    smax = warp_max(smax);
+    // block-wide ranges, bounds and flags: a warp reduction of order-
+    // preserving integer keys (the bounds and their parts are >= 0, so their
+    // bit patterns already order like the values), one slot per warp, then
+    // each warp reduces the slots itself
+    int kv[7] = {f2key(lox), -f2key(hix), f2key(loy), -f2key(hiy), -__float_as_int(bmax), -__float_as_int(rmax),
+                 -__float_as_int(smax)};  // minima (maxima negated; keys of finite values never overflow)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) kv[q] = __reduce_min_sync(kFull, kv[q]);
     const int fz = __any_sync(kFull, zbad), fw = __any_sync(kFull, wild);
     if (lane == 0) {
-        sm.red_f[wp][0] = lox;
-        sm.red_f[wp][1] = hix;
-        sm.red_f[wp][2] = loy;
-        sm.red_f[wp][3] = hiy;
-        sm.red_f[wp][4] = bmax;
-        sm.red_f[wp][5] = rmax;
-        sm.red_f[wp][6] = smax;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) sm.red_k[wp][q] = kv[q];
         sm.red_i[wp][0] = fz;
         sm.red_i[wp][1] = fw;
     }
     __syncthreads();
-    int anyz = 0, anyw = 0;
 #pragma unroll
-    for (int q = 0; q < B::WARPS; ++q) {
-        lox = fminf(lox, sm.red_f[q][0]);
-        hix = fmaxf(hix, sm.red_f[q][1]);
-        loy = fminf(loy, sm.red_f[q][2]);
-        hiy = fmaxf(hiy, sm.red_f[q][3]);
-        bmax = fmaxf(bmax, sm.red_f[q][4]);
-        rmax = fmaxf(rmax, sm.red_f[q][5]);
-        smax = fmaxf(smax, sm.red_f[q][6]);
-        anyz |= sm.red_i[q][0];
-        anyw |= sm.red_i[q][1];
-    }
-    // (red_f / red_i are written again only in the next layer, behind the
+    for (int q = 0; q < 7; ++q) kv[q] = __reduce_min_sync(kFull, lane < B::WARPS ? sm.red_k[lane][q] : INT_MAX);
+    const int anyz = __any_sync(kFull, lane < B::WARPS && sm.red_i[lane][0]);
+    const int anyw = __any_sync(kFull, lane < B::WARPS && sm.red_i[lane][1]);
+    lox = key2f(kv[0]);
+    hix = key2f(-kv[1]);
+    loy = key2f(kv[2]);
+    hiy = key2f(-kv[3]);
+    bmax = __int_as_float(-kv[4]);
+    rmax = __int_as_float(-kv[5]);
+    smax = __int_as_float(-kv[6]);
+    // (red_k / red_i are written again only in the next layer, behind the
     // three barriers below)
     if (anyz) return 1;
     if (anyw) return 2;
@@ -576,10 +581,17 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
     if (lane == 31) sm.wsum[wp] = incl;
     __syncthreads();
     int woff = 0, total = 0;
+    if constexpr (B::WARPS > 2) {  // the warps' offsets by a scan over the lanes
+        const int ws = lane < B::WARPS ? sm.wsum[lane] : 0;
+        const int wi = warp_incl_scan(ws, lane);
+        woff = __shfl_sync(kFull, wi - ws, wp);
+        total = __shfl_sync(kFull, wi, B::WARPS - 1);
+    } else {
 #pragma unroll
-    for (int q = 0; q < B::WARPS; ++q) {
-        woff += q < wp ? sm.wsum[q] : 0;
-        total += sm.wsum[q];
+        for (int q = 0; q < B::WARPS; ++q) {
+            woff += q < wp ? sm.wsum[q] : 0;
+            total += sm.wsum[q];
+        }
     }
     int run = pbase + woff + incl - cnt;
 #pragma unroll
