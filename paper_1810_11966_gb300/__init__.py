@@ -13,7 +13,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libjpsi.so")
+# JPSI_LIBRARY may name another build of the library, e.g. libjpsi_checked.so
+# (bounds-checked stores) beside this file
+LIB_PATH = os.environ.get("JPSI_LIBRARY") or os.path.join(_HERE, "libjpsi.so")
 
 JPSI_OK, JPSI_EINVAL, JPSI_ENOMEM, JPSI_ECAPACITY, JPSI_ECUDA, JPSI_ETIMEOUT, JPSI_EBUSY = range(7)
 JPSI_MODE_PAPER, JPSI_MODE_CHAIN = 0, 1

@@ -1,5 +1,7 @@
-"""Builds libjpsi.so (sm_103a) in-tree with nvcc: two translation units
-compiled in parallel, statically linked CUDA runtime."""
+"""Builds libjpsi.so (sm_103a) in-tree with nvcc, and libjpsi_checked.so, the
+same library with bounds-checked stores (-DJPSI_CHECKED=1) that the tests run
+the parity suite on: every translation unit compiled in parallel, statically
+linked CUDA runtime."""
 from __future__ import annotations
 
 import os
@@ -12,9 +14,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjpsi.so")
+LIB_CHECKED = os.path.join(HERE, "libjpsi_checked.so")
 SOURCES = ["jpsi_kernels.cu", "jpsi_api.cu"]
 # jpsi_kernels.cu once more with the time tests of free-streaming windows
 STREAM_UNIT = ("jpsi_kernels.cu", "jpsi_kernels_stream.o", ["-DJPSI_STREAM=1"])
+# the kernels again with bounds-checked stores (the host code is shared)
+CHECKED_UNITS = [("jpsi_kernels.cu", "jpsi_kernels_checked.o", ["-DJPSI_CHECKED=1"]),
+                 ("jpsi_kernels.cu", "jpsi_kernels_stream_checked.o", ["-DJPSI_STREAM=1", "-DJPSI_CHECKED=1"])]
 HEADERS = ["jpsi_device.cuh", "jpsi_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xptxas", "-v", "-Xcompiler", "-fPIC,-O2",
@@ -29,9 +35,9 @@ def _nvcc():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_CHECKED):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECKED))
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "jpsi.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -54,14 +60,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES] + [STREAM_UNIT]
-    with ThreadPoolExecutor(len(units)) as ex:
-        objs = list(ex.map(compile_one, units))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(len(units) + len(CHECKED_UNITS)) as ex:
+        objs = list(ex.map(compile_one, units + CHECKED_UNITS))
+    api = objs[SOURCES.index("jpsi_api.cu")]
+    plain_objs, checked_objs = objs[:len(units)], [api] + objs[len(units):]
+    for lib, lib_objs in ((LIB, plain_objs), (LIB_CHECKED, checked_objs)):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *lib_objs, "-lpthread"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
+        os.replace(tmp, lib)
     if verbose:
         for src in SOURCES:
             print(open(os.path.join(BUILD, src.replace(".cu", ".log"))).read())

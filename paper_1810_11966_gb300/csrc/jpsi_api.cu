@@ -37,6 +37,9 @@ struct Range {
 };
 
 constexpr size_t kDefaultBudget = (size_t)8 << 30;
+// what a run of the checked build reports when one of its kernels skipped a
+// store outside its array (the normal build never sets the bit)
+constexpr const char* kBoundsMsg = "checked build: a store outside its array was skipped";
 constexpr int kMaxChunks = 8;            // jpsi_run_host pipelines copies and counting in up to 8 chunks
 constexpr int64_t kChunkMinEvents = 65536;
 
@@ -354,6 +357,7 @@ jpsi_status prepare(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outputs
     j.trip_off = o->trip_off ? o->trip_off : (int64_t*)rs.trip_off.p;
     j.block_sums = (int64_t*)rs.block_sums.p;
     j.triplets = o->triplets;
+    j.trip_cap = o->triplets ? o->trip_capacity : 0;
     j.tscr = nullptr;
     j.tscr_cap = 0;
     if (o->triplets && c->tune.record_cap != 0) {
@@ -541,6 +545,7 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
         return cuda_fail(c, e, "ctrl readback");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "count phase");
     const Ctrl ctl = *rs.h_ctrl;
+    if (ctl.status & kStBounds) return fail(c, JPSI_ECUDA, kBoundsMsg);
     if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
     if (ctl.status & kStNoPool) return fail(c, JPSI_ENOMEM, "distinct_hits: candidates exceed the trigger pool");
     o->trip_needed = ctl.trip_total;
@@ -572,6 +577,7 @@ jpsi_status run_device(jpsi_ctx* c, RunState& rs, const jpsi_batch* b, jpsi_outp
     if ((e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "ctrl readback");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "emit phase");
+    if (rs.h_ctrl->status & kStBounds) return fail(c, JPSI_ECUDA, kBoundsMsg);
     if (rs.h_ctrl->status & kStEmitMismatch) return fail(c, JPSI_ECUDA, "internal: emit pass count mismatch");
     add_timing(c, rs, launches, true);
     return JPSI_OK;
@@ -808,6 +814,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(c, e, "count phase");
     const Ctrl ctl = *rs.h_ctrl;
+    if (ctl.status & kStBounds) return fail(c, JPSI_ECUDA, kBoundsMsg);
     if (ctl.status & kStInvalid) return fail(c, JPSI_EINVAL, "malformed offsets or a hit with z <= 0");
     if (ctl.status & kStNoPool) return fail(c, JPSI_ENOMEM, "distinct_hits: candidates exceed the trigger pool");
     ho->trip_needed = ctl.trip_total;
@@ -826,6 +833,7 @@ jpsi_status run_host_pipelined(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, 
         if (e == cudaSuccess) e = cudaMemcpyAsync(rs.h_ctrl, rs.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "emit");
+        if (rs.h_ctrl->status & kStBounds) return fail(c, JPSI_ECUDA, kBoundsMsg);
         if (rs.h_ctrl->status & kStEmitMismatch) return fail(c, JPSI_ECUDA, "internal: emit pass count mismatch");
     }
     e = cudaSuccess;

@@ -15,7 +15,21 @@ enum : int32_t {
     kStEmitMismatch = 2,   // emit pass found a different count than the count pass (internal error)
     kStNoScratch = 4,      // a triplet index did not fit the scratch entry format
     kStNoPool = 8,         // distinct_hits: the candidates' hits found no room in the trigger pool
+    kStBounds = 16,        // checked build: a store with an index outside its array was skipped
 };
+
+// Checked build.  Compiled with -DJPSI_CHECKED=1 (libjpsi_checked.so, which
+// the tests run the parity suite on; the stand-in for a device memory
+// checker), every store whose index comes from data, a scan or a counter
+// tests the index against its array's extent first: JPSI_IN(ctrl, ok) is
+// `ok`, and a false `ok` skips the store and sets kStBounds in the run's
+// status word, which fails the run with JPSI_ECUDA.  In the normal build
+// JPSI_IN is `true` and the test disappears.
+#if defined(JPSI_CHECKED) && JPSI_CHECKED
+#define JPSI_IN(ctrl, ok) ((ok) || (atomicOr(&(ctrl)->status, (int32_t)kStBounds), false))
+#else
+#define JPSI_IN(ctrl, ok) true
+#endif
 
 // Layer-local indices (i, j, k) of a trigger triplet, 21 bits each.
 __host__ __device__ inline unsigned long long pack_ijk(int i, int j, int k) {
@@ -110,6 +124,7 @@ struct Job {
     int64_t* trip_off;            // [n_units + 1]
     int64_t* block_sums;          // scan scratch
     int32_t* triplets;            // may be null
+    int64_t trip_cap;             // rows the triplet buffer holds
     TripEntry* tscr;              // counting-pass triplet entries (null: not recorded)
     int64_t tscr_cap;
     Ctrl* ctrl;

@@ -416,7 +416,7 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         if (key[r] >= 0) {
             const int row = NY > 1 ? slope_bin<NY>(sy[r], loy, scy) : 0;
             const int cell = row * NX + slope_bin<NX>(sx[r], lox, scx);
-            key[r] = (cell << 16) | (int)atomicAdd(&w.cnt[cell], 1u);
+            key[r] = JPSI_IN(j.ctrl, cell >= 0 && cell < NC) ? (cell << 16) | (int)atomicAdd(&w.cnt[cell], 1u) : -1;
         }
     }
     __syncwarp();
@@ -449,8 +449,10 @@ __device__ int stage_layer_warp(const Job& j, WarpTile<Cfg>& w, int l, int32_t b
         if (32 * r >= n) break;
         if (key[r] >= 0) {
             const int pos = bst[key[r] >> 16] + (key[r] & 0xffff);
-            w.P[pos] = make_float2(sx[r], sy[r]);
-            w.idx[pos] = (uint16_t)(lane + 32 * r);
+            if (JPSI_IN(j.ctrl, pos >= 0 && pos < Cfg::HCAP)) {
+                w.P[pos] = make_float2(sx[r], sy[r]);
+                w.idx[pos] = (uint16_t)(lane + 32 * r);
+            }
         }
     }
     if (lane == 0) {
@@ -565,7 +567,7 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         if (B::THREADS * r >= n) break;
         if (key[r] >= 0) {
             const int cell = slope_bin<B::NY>(sy[r], loy, scy) * B::NX + slope_bin<B::NX>(sx[r], lox, scx);
-            key[r] = (cell << 16) | cell_count_add(bst, cell);
+            key[r] = JPSI_IN(j.ctrl, cell >= 0 && cell < B::NC) ? (cell << 16) | cell_count_add(bst, cell) : -1;
         }
     }
     __syncthreads();
@@ -606,8 +608,10 @@ __device__ int stage_layer_block(const Job& j, BlockSmem<B>& sm, int l, int32_t 
         if (B::THREADS * r >= n) break;
         if (key[r] >= 0) {
             const int pos = bst[key[r] >> 16] + (key[r] & 0xffff);
-            sm.P[pos] = make_float2(sx[r], sy[r]);
-            sm.idx[pos] = (uint16_t)(tid + B::THREADS * r);
+            if (JPSI_IN(j.ctrl, pos >= 0 && pos < B::HCAP)) {
+                sm.P[pos] = make_float2(sx[r], sy[r]);
+                sm.idx[pos] = (uint16_t)(tid + B::THREADS * r);
+            }
         }
     }
     if (tid == 0) {
@@ -782,7 +786,8 @@ __device__ __forceinline__ void fit_and_record(const Job& j, const TV& t, int la
             if (lane == 0) b = atomicAdd(sh_rank, np);
             base = __shfl_sync(kFull, b, 0);
         }
-        if (EMIT && ok && base + rk < limit) {  // never past the unit's rows
+        if (EMIT && ok && base + rk < limit &&  // never past the unit's rows
+            JPSI_IN(j.ctrl, (rows - j.triplets) / 3 + base + rk < j.trip_cap)) {
             int32_t* r = rows + 3 * (int64_t)(base + rk);
             r[0] = ii;
             r[1] = jj;
@@ -962,7 +967,8 @@ __device__ int enum_station(const Job& j, const TV& t, uint32_t* queue, int lane
             const bool pass = in & pair_ok(Po.x, Po.y, Pj.x, Pj.y, B01);
             const unsigned mask = __ballot_sync(kFull, pass);
             if (mask) {
-                if (pass) queue[qn + __popc(mask & lanemask_lt())] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
+                const int qi = qn + __popc(mask & lanemask_lt());
+                if (pass && JPSI_IN(j.ctrl, qi < kQCap)) queue[qi] = (uint32_t)(p0 + i0 + o) | ((uint32_t)pj << 16);
                 qn += __popc(mask);
                 if (qn > kQCap - 32) {
                     __syncwarp();
@@ -1173,13 +1179,13 @@ __device__ __forceinline__ void push_event(const Job& j, int64_t e, uint8_t cls)
     if (j.plain) return;  // the one-launch form's block kernel finds the event by its class
     if (cls == kClsMedium) {
         const int gi = atomicAdd(&j.ctrl->n_medium, 1);
-        j.mlist[gi] = (int32_t)e;
+        if (JPSI_IN(j.ctrl, gi < j.n_events)) j.mlist[gi] = (int32_t)e;
     } else if (cls == kClsHeavy) {
         const int gi = atomicAdd(&j.ctrl->n_heavy, 1);
-        j.hlist[gi] = (int32_t)e;
+        if (JPSI_IN(j.ctrl, gi < j.n_events)) j.hlist[gi] = (int32_t)e;
     } else {
         const int gi = atomicAdd(&j.ctrl->n_generic, 1);
-        j.glist[gi] = (int32_t)e;
+        if (JPSI_IN(j.ctrl, gi < j.n_events)) j.glist[gi] = (int32_t)e;
     }
 }
 
@@ -1989,7 +1995,8 @@ __device__ void generic_event(const Job& j, int64_t e, const GenShared& g) {
                 }
                 if (EMIT) {
                     const int pos = atomicAdd(g.s_count, 1);
-                    if (pos < ulimit) {  // never past the unit's rows
+                    if (pos < ulimit &&  // never past the unit's rows
+                        JPSI_IN(j.ctrl, (rows - j.triplets) / 3 + pos < j.trip_cap)) {
                         int32_t* r = rows + 3 * (int64_t)pos;
                         r[0] = (int32_t)i;
                         r[1] = (int32_t)jx;
@@ -2326,7 +2333,9 @@ __global__ void k_scatter(const __grid_constant__ Job j) {
         const int64_t e = te.unit / j.S;
         const unsigned tag = (unsigned)((te.ijk >> kTagShift) & 7u);
         if (j.ev_class[e] != tag) continue;
-        int32_t* r = j.triplets + 3 * (j.trip_off[te.unit] + te.rank);
+        const int64_t row = j.trip_off[te.unit] + te.rank;
+        if (!JPSI_IN(j.ctrl, row >= 0 && row < j.trip_cap)) continue;
+        int32_t* r = j.triplets + 3 * row;
         r[0] = (int32_t)(te.ijk & 0xfffffu);
         r[1] = (int32_t)((te.ijk >> 20) & 0xfffffu);
         r[2] = (int32_t)((te.ijk >> 40) & 0xfffffu);
@@ -2835,6 +2844,7 @@ extern "C" jpsi_status jpsi_select_noalloc(const jpsi_params* p, const jpsi_batc
     Ctrl ctl{};
     if (cudaMemcpyAsync(&ctl, dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return JPSI_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return JPSI_ECUDA;
+    if (ctl.status & kStBounds) return JPSI_ECUDA;  // (checked build only)
     if (ctl.status & kStInvalid) return JPSI_EINVAL;
     // an event beyond the warp tile (or with extreme coordinates) needs the
     // other kernels and their scratch: not available here

@@ -28,6 +28,17 @@ def test_library_exports_every_declared_symbol():
     assert set(jp.EXPORTS) == names
 
 
+def test_checked_build_exports_the_same_symbols():
+    # the bounds-checked build that the GPU tests run the parity suites on
+    import paper_1810_11966_gb300.build as b
+    b.build()
+    lib = ctypes.CDLL(b.LIB_CHECKED)
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+    log = open(os.path.join(b.BUILD, "jpsi_kernels_checked.log")).read()
+    assert "-DJPSI_CHECKED=1" in log.splitlines()[0]
+
+
 def test_strerror_without_gpu():
     import paper_1810_11966_gb300 as jp
     lib = jp.load(build_if_missing=True)
