@@ -312,6 +312,12 @@ def run_timeslices(args, w, dev, jp, torch):
     clk = clocks.stop()
     tp, per_p, _ = sweep(jp.jpsi_run_plain)
     n_ev = int(sizes.sum())
+    # the counting phase of every timeslice (all tiles) against HBM: each hit
+    # read once, offsets, unit and track counts, class bytes
+    alg = algorithmic_bytes(n_ev, n_hits_tot, w.n_stations)
+    count_ms = tm_b.light_ms + tm_b.count_rest_ms
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (count_ms / 1000.0) / 1e9
     line = {"metric": METRIC, "value": n_ev / (tb / 1000), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -322,6 +328,10 @@ def run_timeslices(args, w, dev, jp, torch):
             "speedup_batched_vs_plain": tp / tb,
             "slice_latency_ms": {"batched": percentiles(per_b, (50, 99)), "plain": percentiles(per_p, (50, 99))},
             "phases_ms": {"light_count": tm_b.light_ms, "count_rest": tm_b.count_rest_ms, "emit": tm_b.emit_ms},
+            "roofline": {"bound": "hbm", "kernel": "counting phase (k_light, k_medium, k_sort_heavy, k_heavy, "
+                         "k_heavy_units, k_heavy_final, k_generic, k_accept, scan)", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes": alg},
             "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)

@@ -254,16 +254,16 @@ jpsi_status jpsi_autotune(jpsi_ctx *ctx, const jpsi_batch *sample);
  * jpsi_serve_start reserves `n_slots`
  * resident slots whose device buffers fit `slot_hits` hits, `slot_events`
  * events and `slot_triplets` triplets each, within the context's budget.
- * jpsi_serve_submit copies one HOST batch into a free slot on a copy stream
- * and runs it on one of the compute streams as soon as a slot is free (it
- * blocks while all slots are busy: back-pressure, nothing is dropped);
- * outputs are copied back into the HOST `out` buffers, which must stay valid
- * until jpsi_serve_wait returns for the ticket.  Each result is identical to
- * jpsi_run on the same batch alone. */
+ * jpsi_serve_submit copies one batch into a free slot and runs it on the
+ * slot's stream as soon as a slot is free (it blocks while all slots are busy:
+ * back-pressure, nothing is dropped); the outputs are copied back into `out`.
+ * The batch's arrays and the outputs may each be in host memory or in device
+ * memory of the context's device (the copies follow the pointers); they must
+ * stay valid until jpsi_serve_wait returns for the ticket.  Each result is
+ * identical to jpsi_run on the same batch alone. */
 jpsi_status jpsi_serve_start(jpsi_ctx *ctx, int n_slots, int64_t slot_events, int64_t slot_hits,
                              int64_t slot_triplets);
-jpsi_status jpsi_serve_submit(jpsi_ctx *ctx, const jpsi_batch *host_batch, jpsi_outputs *host_out,
-                              uint64_t *ticket);
+jpsi_status jpsi_serve_submit(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, uint64_t *ticket);
 /* Waits at most timeout_ms (< 0: no limit) for `ticket`; on completion writes
  * the run's status and its latency (submit -> outputs in host memory). */
 jpsi_status jpsi_serve_wait(jpsi_ctx *ctx, uint64_t ticket, int timeout_ms, jpsi_status *result,

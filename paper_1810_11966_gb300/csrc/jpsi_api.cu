@@ -604,7 +604,9 @@ void apply_tuning(jpsi_ctx* c) {
     ++c->cfg_id;
 }
 
-// Copies H2D of a host batch into device buffers `x, y, z, off`.
+// Copies a batch into device buffers `x, y, z, off`: from host memory, or
+// (serving) from device memory of the context's device; the direction of each
+// copy follows from the pointer (unified addressing).
 jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevBuf& z, DevBuf& off, DevBuf& ztab,
                    jpsi_batch* db, cudaStream_t st) {
     const int64_t S = c->p.n_stations;
@@ -616,15 +618,15 @@ jpsi_status upload(jpsi_ctx* c, const jpsi_batch* hb, DevBuf& x, DevBuf& y, DevB
         return s;
     cudaError_t e = cudaSuccess;
     if (hb_bytes) {
-        if (e == cudaSuccess) e = cudaMemcpyAsync(x.p, hb->x, hb_bytes, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(y.p, hb->y, hb_bytes, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && hb->z) e = cudaMemcpyAsync(z.p, hb->z, hb_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(x.p, hb->x, hb_bytes, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(y.p, hb->y, hb_bytes, cudaMemcpyDefault, st);
+        if (e == cudaSuccess && hb->z) e = cudaMemcpyAsync(z.p, hb->z, hb_bytes, cudaMemcpyDefault, st);
     }
-    if (e == cudaSuccess && hb->n_events > 0) e = cudaMemcpyAsync(off.p, hb->offsets, ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && hb->n_events > 0) e = cudaMemcpyAsync(off.p, hb->offsets, ob, cudaMemcpyDefault, st);
     if (e == cudaSuccess && !hb->z && hb_bytes) {
         // per-hit z filled on the device from the geometry table
         if ((s = ensure(c, ztab, (size_t)S * 3 * 4, "z table")) != JPSI_OK) return s;
-        e = cudaMemcpyAsync(ztab.p, hb->z_layer, (size_t)S * 3 * 4, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(ztab.p, hb->z_layer, (size_t)S * 3 * 4, cudaMemcpyDefault, st);
         if (e == cudaSuccess)
             e = launch_expand_z((const int32_t*)off.p, (const float*)ztab.p, (float*)z.p, 0, hb->n_events, (int)S,
                                 hb->n_hits, c->n_sm, st);
@@ -698,14 +700,15 @@ jpsi_status run_host_with(jpsi_ctx* c, RunState& rs, const jpsi_batch* hb, jpsi_
     ho->trip_needed = dout.trip_needed;
     if (s != JPSI_OK && s != JPSI_ECAPACITY) return s;
     cudaError_t e = cudaSuccess;
+    // outputs to host memory, or (serving) to device memory
     if (ho->accept_bits && ne > 0)
-        e = cudaMemcpyAsync(ho->accept_bits, acc.p, (size_t)((ne + 31) / 32) * 4, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ho->accept_bits, acc.p, (size_t)((ne + 31) / 32) * 4, cudaMemcpyDefault, st);
     if (e == cudaSuccess && ho->track_counts && ne > 0)
-        e = cudaMemcpyAsync(ho->track_counts, tc.p, (size_t)ne * 4, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ho->track_counts, tc.p, (size_t)ne * 4, cudaMemcpyDefault, st);
     if (e == cudaSuccess && ho->trip_off)
-        e = cudaMemcpyAsync(ho->trip_off, toff.p, (size_t)(nu + 1) * 8, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ho->trip_off, toff.p, (size_t)(nu + 1) * 8, cudaMemcpyDefault, st);
     if (e == cudaSuccess && ho->triplets && s == JPSI_OK && dout.trip_needed > 0)
-        e = cudaMemcpyAsync(ho->triplets, trip.p, (size_t)dout.trip_needed * 12, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ho->triplets, trip.p, (size_t)dout.trip_needed * 12, cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "output download");
     return s;

@@ -94,3 +94,36 @@ def test_serving_rejects_oversized_request(lib, synth_mod):
     s, _ = lib.jpsi_serve_submit(ctx.ctx, hb, o)
     assert s == lib.JPSI_EINVAL
     assert lib.jpsi_serve_stop(ctx.ctx) == 0
+
+
+def test_serving_device_batch_and_outputs(lib, synth_mod, oracle_mod):
+    # a batch and outputs in device memory of the context's device: the slot
+    # copies device to device, and the result equals the oracle's
+    import torch
+    S = 4
+    b = synth_mod.generate("lognormal_timeslices", 0, 1200)
+    ref = oracle_mod.run(oracle_mod.params(S, 1, t_xz=0.25), b, n_threads=8)
+    cap = int(ref["trip_needed"])
+    n, nu = b["n_events"], b["n_events"] * S
+    ctx = lib.Context(lib.params(S, 1, t_xz=0.25))
+    assert lib.jpsi_serve_start(ctx.ctx, 2, n, b["n_hits"], cap) == 0
+    d = {k: torch.from_numpy(b[k]).cuda() for k in ("x", "y", "z", "offsets")}
+    hb = lib.make_batch(d["x"], d["y"], d["z"], d["offsets"], n, b["n_hits"])
+    acc = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
+    tc = torch.zeros(n, dtype=torch.int32, device="cuda")
+    toff = torch.zeros(nu + 1, dtype=torch.int64, device="cuda")
+    trip = torch.zeros((max(cap, 1), 3), dtype=torch.int32, device="cuda")
+    o = lib.jpsi_outputs()
+    o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
+    o.triplets, o.trip_capacity = trip.data_ptr(), max(cap, 1)
+    torch.cuda.synchronize()
+    s, t = lib.jpsi_serve_submit(ctx.ctx, hb, o)
+    assert s == 0
+    ws, rs, _ = lib.jpsi_serve_wait(ctx.ctx, t, 60000)
+    assert ws == 0 and rs == 0 and o.trip_needed == cap
+    assert np.array_equal(acc.cpu().numpy().view(np.uint32), ref["accept_bits"])
+    assert np.array_equal(tc.cpu().numpy(), ref["track_counts"])
+    assert np.array_equal(toff.cpu().numpy(), ref["trip_off"])
+    assert np.array_equal(sorted_triplets(toff.cpu().numpy(), trip.cpu().numpy()[:cap], nu),
+                          sorted_triplets(ref["trip_off"], ref["triplets"], nu))
+    assert lib.jpsi_serve_stop(ctx.ctx) == 0
