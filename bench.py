@@ -252,10 +252,72 @@ def percentiles(v, qs=(50, 99, 99.9)):
     return {f"p{q:g}": float(a[min(len(a) - 1, int(np.ceil(q / 100 * len(a))) - 1)]) for q in qs}
 
 
+def serve_slices_from_device(args, jp, torch, dev, p, slices):
+    """The same device-resident timeslices served through jpsi_serve_* with
+    device batches and device outputs: while one slot waits on its host
+    round trips or its kernels' tails, another slot's kernels run.  The slots
+    read the timeslices and write the outputs in place.  One untimed pass (graph
+    capture in every slot), then three timed passes of all timeslices, each
+    from the first submit to the last completion (host wall clock, the device
+    synchronised before); every served result is compared with the jpsi_run
+    sweep's outputs (accept bits, track counts, offsets, and the triplet rows
+    of each unit as a set: their order inside a unit is unspecified)."""
+    torch.cuda.synchronize()
+
+    def canon(s_):  # accept bits, counts, offsets, and the rows sorted inside each unit
+        toff, n = s_[5], int(s_[2].trip_needed)
+        rows = s_[6][:n].to(torch.int64)
+        unit = torch.repeat_interleave(torch.arange(toff.numel() - 1, device=toff.device), toff[1:] - toff[:-1])
+        order = torch.arange(n, device=rows.device)
+        for key in (rows[:, 2], rows[:, 1], rows[:, 0], unit):  # stable sorts, least significant key first
+            order = order[torch.sort(key[order], stable=True)[1]]
+        return s_[3].clone(), s_[4].clone(), toff.clone(), rows[order]
+
+    ref = [canon(s_) for s_ in slices]
+    ctx = jp.Context(p, device=dev.index, hbm_budget=64 << 30)
+    ev_max = max(int(s_[1].n_events) for s_ in slices)
+    hits_max = max(int(s_[1].n_hits) for s_ in slices)
+    cap = max(int(s_[2].trip_needed) for s_ in slices)
+    ctx.check(jp.jpsi_serve_start(ctx.ctx, args.slots, ev_max, hits_max, cap))
+
+    def one_pass():
+        tickets, lat = [], []
+        for s_ in slices:  # a submit blocks while every slot is busy
+            s, tk = jp.jpsi_serve_submit(ctx.ctx, s_[1], s_[2])
+            ctx.check(s)
+            tickets.append(tk)
+        for tk in tickets:
+            ws, rs, lt = jp.jpsi_serve_wait(ctx.ctx, tk, 60000)
+            ctx.check(ws)
+            ctx.check(rs)
+            lat.append(lt * 1000.0)
+        return lat
+
+    one_pass()
+    torch.cuda.synchronize()
+    ms, lat = [], []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        lat += one_pass()
+        ms.append((time.perf_counter() - t0) * 1000.0)
+    torch.cuda.synchronize()
+    same = all(all(torch.equal(a, b) for a, b in zip(r, canon(s_))) for r, s_ in zip(ref, slices))
+    ctx.check(jp.jpsi_serve_stop(ctx.ctx))
+    ctx.close()
+    n_ev = sum(int(s_[1].n_events) for s_ in slices)
+    med = statistics.median(ms)
+    return {"value": n_ev / (med / 1000.0), "unit": UNIT, "ms_total_median": med, "ms_total_passes": ms,
+            "slots": args.slots, "slot_latency_ms": percentiles(lat, (50, 99)),
+            "equal_to_jpsi_run": bool(same),
+            "timing": "host wall clock per pass of every timeslice, first submit to last completion; "
+                      "batches and outputs in device memory, used in place by the slots; median of 3 passes"}
+
+
 def run_timeslices(args, w, dev, jp, torch):
     """Uneven timeslices (log-normal multiplicities): one jpsi_run per
     timeslice (persistent kernels replayed from the captured graph) against
-    one jpsi_run_plain per timeslice, all data resident."""
+    one jpsi_run_plain per timeslice, all data resident; beside them the same
+    timeslices served from device memory over the serving slots."""
     import synth
     sizes = synth.timeslice_sizes(w, args.slices)
     starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
@@ -311,6 +373,11 @@ def run_timeslices(args, w, dev, jp, torch):
     tb, per_b, tm_b = sweep(jp.jpsi_run)
     clk = clocks.stop()
     tp, per_p, _ = sweep(jp.jpsi_run_plain)
+    ctx.close()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    served = serve_slices_from_device(args, jp, torch, dev, p, slices)
+    served["clocks"] = clocks.stop()
     n_ev = int(sizes.sum())
     # the counting phase of every timeslice (all tiles) against HBM: each hit
     # read once, offsets, unit and track counts, class bytes
@@ -332,11 +399,11 @@ def run_timeslices(args, w, dev, jp, torch):
                          "k_heavy_units, k_heavy_final, k_generic, k_accept, scan)", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "algorithmic_bytes": alg},
+            "served_from_device": served,
             "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def run_free_stream(args, w, dev, jp, torch):

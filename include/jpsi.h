@@ -254,13 +254,16 @@ jpsi_status jpsi_autotune(jpsi_ctx *ctx, const jpsi_batch *sample);
  * jpsi_serve_start reserves `n_slots`
  * resident slots whose device buffers fit `slot_hits` hits, `slot_events`
  * events and `slot_triplets` triplets each, within the context's budget.
- * jpsi_serve_submit copies one batch into a free slot and runs it on the
- * slot's stream as soon as a slot is free (it blocks while all slots are busy:
- * back-pressure, nothing is dropped); the outputs are copied back into `out`.
- * The batch's arrays and the outputs may each be in host memory or in device
- * memory of the context's device (the copies follow the pointers); they must
- * stay valid until jpsi_serve_wait returns for the ticket.  Each result is
- * identical to jpsi_run on the same batch alone. */
+ * jpsi_serve_submit hands one batch to a free slot, which runs it on its own
+ * stream (the call blocks while all slots are busy: back-pressure, nothing is
+ * dropped).  The batch's arrays and the outputs may each be in host memory or
+ * in device memory of the context's device.  When all of them are in device
+ * memory of that device the slot reads and writes them in place, as jpsi_run
+ * does; otherwise it copies the batch into its resident buffers and the
+ * outputs back into `out` (the copies follow the pointers).  They must stay
+ * valid until jpsi_serve_wait returns for the ticket.  Each result is
+ * identical to jpsi_run on the same batch alone (the order of rows inside a
+ * unit is unspecified, as for jpsi_run). */
 jpsi_status jpsi_serve_start(jpsi_ctx *ctx, int n_slots, int64_t slot_events, int64_t slot_hits,
                              int64_t slot_triplets);
 jpsi_status jpsi_serve_submit(jpsi_ctx *ctx, const jpsi_batch *batch, jpsi_outputs *out, uint64_t *ticket);

@@ -13,6 +13,7 @@
 #include <cstddef>
 #include <cstring>
 #include <deque>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1248,6 +1249,20 @@ jpsi_status jpsi_autotune(jpsi_ctx* c, const jpsi_batch* sample) {
 
 // ------------------------------------------------------------- serving
 
+// True when every non-null pointer is device memory of `device`.
+static bool all_on_device(std::initializer_list<const void*> ps, int device) {
+    for (const void* p : ps) {
+        if (!p) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeDevice || a.device != device) return false;
+    }
+    return true;
+}
+
 static void slot_worker(jpsi_ctx* c, int si) {
     cudaSetDevice(c->device);
     Slot* sl = c->slots[si];
@@ -1259,8 +1274,14 @@ static void slot_worker(jpsi_ctx* c, int si) {
         jpsi_outputs* o = sl->out;
         lk.unlock();
         Range r("jpsi_serve slot run");
+        // a batch and outputs that are all in this device's memory are used
+        // in place, as jpsi_run uses them; otherwise the slot's own buffers
+        // take copies
+        const bool in_place = all_on_device(
+            {b.x, b.y, b.z, b.offsets, o->accept_bits, o->track_counts, o->trip_off, o->triplets}, c->device);
         auto run_once = [&]() -> jpsi_status {
             if (take_fault(c->fault_run)) return fail(c, JPSI_ECUDA, "injected run failure");
+            if (in_place) return run_device(c, sl->rs, &b, o, sl->stream, true);
             return run_host_with(c, sl->rs, &b, o, sl->x, sl->y, sl->z, sl->off, sl->accept, sl->tracks,
                                  sl->trip_off, sl->triplets, sl->cap_trip, sl->stream);
         };

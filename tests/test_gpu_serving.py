@@ -96,9 +96,11 @@ def test_serving_rejects_oversized_request(lib, synth_mod):
     assert lib.jpsi_serve_stop(ctx.ctx) == 0
 
 
-def test_serving_device_batch_and_outputs(lib, synth_mod, oracle_mod):
-    # a batch and outputs in device memory of the context's device: the slot
-    # copies device to device, and the result equals the oracle's
+@pytest.mark.parametrize("batch_on,out_on", [("cuda", "cuda"), ("cuda", "cpu"), ("cpu", "cuda")])
+def test_serving_device_batch_and_outputs(lib, synth_mod, oracle_mod, batch_on, out_on):
+    # a batch and outputs in device memory of the context's device are used
+    # in place; with either of them in host memory the slot copies; every
+    # result equals the oracle's
     import torch
     S = 4
     b = synth_mod.generate("lognormal_timeslices", 0, 1200)
@@ -107,12 +109,17 @@ def test_serving_device_batch_and_outputs(lib, synth_mod, oracle_mod):
     n, nu = b["n_events"], b["n_events"] * S
     ctx = lib.Context(lib.params(S, 1, t_xz=0.25))
     assert lib.jpsi_serve_start(ctx.ctx, 2, n, b["n_hits"], cap) == 0
-    d = {k: torch.from_numpy(b[k]).cuda() for k in ("x", "y", "z", "offsets")}
+    pin = out_on == "cpu"
+
+    def put(a):
+        return a.cuda() if batch_on == "cuda" else a.pin_memory()
+
+    d = {k: put(torch.from_numpy(b[k])) for k in ("x", "y", "z", "offsets")}
     hb = lib.make_batch(d["x"], d["y"], d["z"], d["offsets"], n, b["n_hits"])
-    acc = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
-    tc = torch.zeros(n, dtype=torch.int32, device="cuda")
-    toff = torch.zeros(nu + 1, dtype=torch.int64, device="cuda")
-    trip = torch.zeros((max(cap, 1), 3), dtype=torch.int32, device="cuda")
+    acc = torch.zeros((n + 31) // 32, dtype=torch.int32, device=out_on, pin_memory=pin)
+    tc = torch.zeros(n, dtype=torch.int32, device=out_on, pin_memory=pin)
+    toff = torch.zeros(nu + 1, dtype=torch.int64, device=out_on, pin_memory=pin)
+    trip = torch.zeros((max(cap, 1), 3), dtype=torch.int32, device=out_on, pin_memory=pin)
     o = lib.jpsi_outputs()
     o.accept_bits, o.track_counts, o.trip_off = acc.data_ptr(), tc.data_ptr(), toff.data_ptr()
     o.triplets, o.trip_capacity = trip.data_ptr(), max(cap, 1)
