@@ -383,6 +383,7 @@ def run_timeslices(args, w, dev, jp, torch):
     # read once, offsets, unit and track counts, class bytes
     alg = algorithmic_bytes(n_ev, n_hits_tot, w.n_stations)
     count_ms = tm_b.light_ms + tm_b.count_rest_ms
+    tpe = ncu_traffic("counting_phase", w.name)
     peak, peak_kind = measured_peaks()
     achieved = alg / (count_ms / 1000.0) / 1e9
     line = {"metric": METRIC, "value": n_ev / (tb / 1000), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -398,7 +399,11 @@ def run_timeslices(args, w, dev, jp, torch):
             "roofline": {"bound": "hbm", "kernel": "counting phase (k_light, k_medium, k_sort_heavy, k_heavy, "
                          "k_heavy_units, k_heavy_final, k_generic, k_accept, scan)", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "algorithmic_bytes": alg},
+                         "traffic": None if tpe is None else tpe * n_ev, "algorithmic_bytes": alg,
+                         "per_event_figures": "ncu on the counting pass of timeslice 0, scaled by the events",
+                         "issue": issue_roofline(ncu_record("counting_phase", w.name, "inst_per_event"), n_ev,
+                                                 count_ms, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                                 clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)},
             "served_from_device": served,
             "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
     if not args.no_cpu_baseline:
