@@ -252,6 +252,20 @@ def percentiles(v, qs=(50, 99, 99.9)):
     return {f"p{q:g}": float(a[min(len(a) - 1, int(np.ceil(q / 100 * len(a))) - 1)]) for q in qs}
 
 
+def canonical_rows(torch, trip_off, rows):
+    """Triplet rows (n x 3) grouped by unit through the CSR `trip_off`, each
+    unit's rows sorted lexicographically: equal for two outputs exactly when
+    they hold the same rows per unit, whatever their order inside a unit."""
+    rows = rows.to(torch.int64)
+    n = rows.shape[0]
+    unit = torch.repeat_interleave(torch.arange(trip_off.numel() - 1, device=trip_off.device),
+                                   trip_off[1:] - trip_off[:-1])
+    order = torch.arange(n, device=rows.device)
+    for key in (rows[:, 2], rows[:, 1], rows[:, 0], unit):  # stable sorts, least significant key first
+        order = order[torch.sort(key[order], stable=True)[1]]
+    return rows[order]
+
+
 def serve_slices_from_device(args, jp, torch, dev, p, slices):
     """The same device-resident timeslices served through jpsi_serve_* with
     device batches and device outputs: while one slot waits on its host
@@ -266,12 +280,7 @@ def serve_slices_from_device(args, jp, torch, dev, p, slices):
 
     def canon(s_):  # accept bits, counts, offsets, and the rows sorted inside each unit
         toff, n = s_[5], int(s_[2].trip_needed)
-        rows = s_[6][:n].to(torch.int64)
-        unit = torch.repeat_interleave(torch.arange(toff.numel() - 1, device=toff.device), toff[1:] - toff[:-1])
-        order = torch.arange(n, device=rows.device)
-        for key in (rows[:, 2], rows[:, 1], rows[:, 0], unit):  # stable sorts, least significant key first
-            order = order[torch.sort(key[order], stable=True)[1]]
-        return s_[3].clone(), s_[4].clone(), toff.clone(), rows[order]
+        return s_[3].clone(), s_[4].clone(), toff.clone(), canonical_rows(torch, toff, s_[6][:n])
 
     ref = [canon(s_) for s_ in slices]
     ctx = jp.Context(p, device=dev.index, hbm_budget=64 << 30)

@@ -1,6 +1,7 @@
-"""bench.py's reference arm (the oracle on the host cores) runs without a GPU:
-its JSON line carries the contract's keys, and under torchrun with two ranks
-only rank 0 works and prints."""
+"""bench.py on the CPU: the reference arm (the oracle on the host cores) runs
+without a GPU, its JSON line carries the contract's keys, and under torchrun
+with two ranks only rank 0 works and prints; the served-from-device check's
+canonical form of triplet rows ignores their order inside a unit."""
 import json
 import os
 import socket
@@ -38,3 +39,28 @@ def test_reference_arm_two_ranks_print_once():
                                   cwd=ROOT, text=True, timeout=600, stderr=subprocess.DEVNULL)
     (line,) = _lines(out)
     assert line["impl"] == "reference" and line["n_gpus"] == 2
+
+
+def test_canonical_rows_ignore_order_inside_a_unit():
+    # the served-from-device check compares triplet rows per unit as sets
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(5)
+    counts = np.array([3, 0, 5, 1, 4])
+    toff = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64))
+    rows = torch.from_numpy(rng.integers(0, 4, size=(int(counts.sum()), 3)).astype(np.int32))
+    base = bench.canonical_rows(torch, toff, rows)
+    # each unit's rows permuted: the same canonical form
+    perm = np.concatenate([o + rng.permutation(c) for o, c in zip(toff[:-1].numpy(), counts)]).astype(np.int64)
+    assert torch.equal(bench.canonical_rows(torch, toff, rows[torch.from_numpy(perm)]), base)
+    # each unit's rows sorted lexicographically, units in order
+    for u, c in enumerate(counts):
+        seg = base[int(toff[u]): int(toff[u]) + c].tolist()
+        assert seg == sorted(seg) and sorted(seg) == sorted(rows[int(toff[u]): int(toff[u]) + c].tolist())
+    # one changed value changes it (the unit boundaries are the offsets,
+    # which the check compares on their own)
+    changed = rows.clone()
+    changed[4, 1] += 1
+    assert not torch.equal(bench.canonical_rows(torch, toff, changed), base)
