@@ -266,7 +266,7 @@ def canonical_rows(torch, trip_off, rows):
     return rows[order]
 
 
-def serve_slices_from_device(args, jp, torch, dev, p, slices):
+def serve_slices_from_device(jp, torch, dev, p, slices, n_slots):
     """The same device-resident timeslices served through jpsi_serve_* with
     device batches and device outputs: while one slot waits on its host
     round trips or its kernels' tails, another slot's kernels run.  The slots
@@ -287,7 +287,7 @@ def serve_slices_from_device(args, jp, torch, dev, p, slices):
     ev_max = max(int(s_[1].n_events) for s_ in slices)
     hits_max = max(int(s_[1].n_hits) for s_ in slices)
     cap = max(int(s_[2].trip_needed) for s_ in slices)
-    ctx.check(jp.jpsi_serve_start(ctx.ctx, args.slots, ev_max, hits_max, cap))
+    ctx.check(jp.jpsi_serve_start(ctx.ctx, n_slots, ev_max, hits_max, cap))
 
     def one_pass():
         tickets, lat = [], []
@@ -316,7 +316,7 @@ def serve_slices_from_device(args, jp, torch, dev, p, slices):
     n_ev = sum(int(s_[1].n_events) for s_ in slices)
     med = statistics.median(ms)
     return {"value": n_ev / (med / 1000.0), "unit": UNIT, "ms_total_median": med, "ms_total_passes": ms,
-            "slots": args.slots, "slot_latency_ms": percentiles(lat, (50, 99)),
+            "slots": n_slots, "slot_latency_ms": percentiles(lat, (50, 99)),
             "equal_to_jpsi_run": bool(same),
             "timing": "host wall clock per pass of every timeslice, first submit to last completion; "
                       "batches and outputs in device memory, used in place by the slots; median of 3 passes"}
@@ -385,7 +385,9 @@ def run_timeslices(args, w, dev, jp, torch):
     ctx.close()
     clocks = Clocks(dev.index)
     clocks.start()
-    served = serve_slices_from_device(args, jp, torch, dev, p, slices)
+    slot_counts = [int(v) for v in args.served_slots.split(",")] if args.served_slots else [args.slots]
+    by_slots = {n: serve_slices_from_device(jp, torch, dev, p, slices, n) for n in slot_counts}
+    served = by_slots.get(args.slots, by_slots[slot_counts[0]])
     served["clocks"] = clocks.stop()
     n_ev = int(sizes.sum())
     # the counting phase of every timeslice (all tiles) against HBM: each hit
@@ -414,6 +416,8 @@ def run_timeslices(args, w, dev, jp, torch):
                                                  count_ms, torch.cuda.get_device_properties(dev).multi_processor_count,
                                                  clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)},
             "served_from_device": served,
+            "served_by_slots": {str(n): {k: r[k] for k in ("value", "ms_total_median", "slot_latency_ms",
+                                                          "equal_to_jpsi_run")} for n, r in by_slots.items()},
             "gpu_launches": int(tm_b.kernel_launches), "clocks": clk, "generate_s": gen_s}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.name, params_kw(args, w), 20_000, n_single=2_000)
@@ -827,6 +831,8 @@ def main():
     ap.add_argument("--stress-budget-gb", type=int, default=160)
     ap.add_argument("--pool", type=int, default=8, help="distinct timeslices generated for the stream workload")
     ap.add_argument("--slots", type=int, default=5)
+    ap.add_argument("--served-slots", default=None,
+                    help="timeslice workload: comma-separated slot counts to serve from device memory (default: --slots)")
     ap.add_argument("--requests", type=int, default=1000, help="requests per offered load (stream workload)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--cpu-windows", type=int, default=12, help="windows of the stream workload's CPU sample")
