@@ -1,7 +1,8 @@
 """bench.py on the CPU: the reference arm (the oracle on the host cores) runs
 without a GPU, its JSON line carries the contract's keys, and under torchrun
 with two ranks only rank 0 works and prints; the served-from-device check's
-canonical form of triplet rows ignores their order inside a unit."""
+canonical form of triplet rows ignores their order inside a unit; the
+roofline arithmetic (algorithmic bytes, issue-slot peak) is the stated one."""
 import json
 import os
 import socket
@@ -64,3 +65,26 @@ def test_canonical_rows_ignore_order_inside_a_unit():
     changed = rows.clone()
     changed[4, 1] += 1
     assert not torch.equal(bench.canonical_rows(torch, toff, changed), base)
+
+
+def test_roofline_arithmetic():
+    # algorithmic bytes: each hit once (x, y, z), the CSR offsets, per-unit and
+    # track counts and the class byte; PAPER mode: the trigger station only
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    S, n = 4, 2
+    assert bench.algorithmic_bytes(n, 10, S) == 12 * 10 + 4 * (n * 3 * S + 1) + 4 * n * S + 4 * n + n
+    # two events, 4 stations x 3 layers; trigger station 3 holds 1 + 2 + 0 and 3 + 0 + 1 hits
+    counts = np.zeros((n, S, 3), np.int64)
+    counts[0, 3] = (1, 2, 0)
+    counts[1, 3] = (3, 0, 1)
+    counts[:, :3] = 5
+    off = np.concatenate([[0], np.cumsum(counts.ravel())]).astype(np.int32)
+    assert bench.algorithmic_bytes(n, int(off[-1]), S, offsets=off, trigger=3) == \
+        12 * 7 + 4 * 4 * n + 4 * n * S + 4 * n + n
+    r = bench.issue_roofline(1000.0, 2_000_000, 2.0, 152, 2070.0)
+    assert r["peak"] == 152 * 4 * 2070e6
+    assert abs(r["achieved"] - 1000.0 * 2_000_000 / 0.002) < 1e-3 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert bench.issue_roofline(None, 1, 1.0, 152, 2070.0)["frac"] is None
